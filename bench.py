@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the FB-LISA hot path on GB300: prints ONE JSON line.
+
+A step is one FB-LISA iteration (Algorithm 1, Steps 2a-2d): mini-batch
+selection, the residual projection and f_N(x), the gradient backprojection,
+and the backtracking loop of prox + trial-objective projections until (2.3)
+holds.  Default workload: 512^3 volume, 720 views, 768x768 detector,
+40-view mini-batches, FP32 storage (synthetic ellipsoid phantom with
+texture; data = A x_true + 1% Gaussian noise).
+
+metric: GUPS = (ray-samples of every forward projection in the step +
+voxel-views of its backprojection) / step time.  A forward projection of
+N_t views counts N_t * nu * nv * N samples (N planes per ray); the
+backprojection counts N_t * N^3 voxel-views.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the method does not shard here; each rank runs an independent
+replica (replicas only), value = all ranks' units / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GUPS fwd+back at 512^3/720 views; FB-LISA time-to-1e-3 rel-err vs plain FP32"
+UNIT = "GUPS"
+OPS_PER_SAMPLE = 14      # FP32 ops of one Joseph sample (K1)
+K3_BYTES_PER_VOXEL = 16  # read x, g; write x_bar in two layouts (FP32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c3_512")
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(gpu_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_data(fbl, wl, device):
+    import numpy as np
+    import torch
+    import synth
+    g = wl.geom
+    xt = synth.phantom(g, wl.n_ellipsoids, wl.seed_phantom, inclusions=wl.inclusions,
+                       texture_std=wl.texture_std)
+    G = fbl.geometry_create(g)
+    xt_d = torch.from_numpy(xt).to(device)
+    b = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
+    chunk = 90
+    for v0 in range(0, g.n_views, chunk):
+        vs = list(range(v0, min(g.n_views, v0 + chunk)))
+        fbl.project(G, xt_d, vs, y=b[v0:v0 + len(vs)])
+    torch.cuda.synchronize(device)
+    if wl.noise == "poisson":
+        bh = synth.poisson_log_data(b.cpu().numpy(), wl.I0, wl.seed_noise)
+        b.copy_(torch.from_numpy(bh))
+    else:
+        sigma = wl.noise_rel * float(b.max())
+        n = synth.gaussian_noise(tuple(b.shape), sigma, wl.seed_noise)
+        b += torch.from_numpy(n).to(device)
+    del xt_d
+    return G, xt, b
+
+
+def step_units(st, g):
+    N_t = st["N_t"]
+    n_proj = st["backtracks"] + 2
+    samples = n_proj * N_t * g.nu * g.nv * g.nx
+    voxel_views = N_t * g.nx * g.ny * g.nz
+    return samples + voxel_views
+
+
+def active_samples(g, views):
+    """Ray-plane samples K1 actually takes for these views (planes where the
+    crossing lies inside (-1, Nb) x (-1, nz)), from the geometry in float64."""
+    import math
+    import numpy as np
+    cu, cv = 0.5 * (g.nu - 1), 0.5 * (g.nv - 1)
+    V = (g.vx, g.vy, g.vz)
+    Nn = (g.nx, g.ny, g.nz)
+    total = 0
+    for v in views:
+        th = 2.0 * math.pi * v / g.n_views if g.angles is None else g.angles[v]
+        c, s_ = math.cos(th), math.sin(th)
+        src = (g.sod * c, g.sod * s_)
+        u = (np.arange(g.nu) - cu) * g.du
+        off = g.sdd - g.sod
+        dx = -off * c - u * s_ - src[0]
+        dy = -off * s_ + u * c - src[1]
+        fam = (np.abs(dy) > np.abs(dx)).astype(int)
+        for f in (0, 1):
+            sel = fam == f
+            if not sel.any():
+                continue
+            a, b = f, 1 - f
+            da = (dx, dy)[a][sel]
+            db = (dx, dy)[b][sel]
+            ca, cb = 0.5 * (Nn[a] - 1), 0.5 * (Nn[b] - 1)
+            p0 = -ca * V[a] - src[a]
+            qb1 = V[a] * db / (da * V[b])
+            qb0 = (src[b] + p0 * db / da) / V[b] + cb
+            zc1 = V[a] / (da * V[2])
+            zc0 = p0 / (da * V[2])
+            w = (np.arange(g.nv) - cv) * g.dv
+            m = np.arange(Nn[a])[:, None]
+            inb = ((qb0[None] + m * qb1[None]) > -1) & ((qb0[None] + m * qb1[None]) < Nn[b])
+            # q_z per (m, column, row): count inside per column via the row range
+            Z = zc0[None] + m * zc1[None]                       # [m, col]
+            qz_lo = (-1 - 0.5 * (g.nz - 1)) / np.where(Z == 0, 1e-30, Z)
+            qz_hi = (g.nz - 0.5 * (g.nz - 1)) / np.where(Z == 0, 1e-30, Z)
+            # rows with -1 < w*Z + cz < nz  <=>  qz_lo < w < qz_hi (Z > 0)
+            lo = np.searchsorted(w, qz_lo, side="right")
+            hi = np.searchsorted(w, qz_hi, side="left")
+            rows = np.clip(hi - lo, 0, None)
+            total += int((rows * inb).sum())
+    return total
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2605_12085_gb300 as fbl
+    import synth
+
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS[args.workload]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    params = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
+                                max_backtracks=60)
+    S = fbl.fblisa_create(G, params)
+    x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        S.step(x, b)
+    S.profile(True)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local_rank)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    stats, batches = [], []
+    for _ in range(args.steps):
+        stats.append(S.step(x, b))
+        batches.append(S.last_batch())
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = S.profile(False)
+    units = sum(step_units(st, g) for st in stats)
+    ms_max, units_all = ms, units
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(units)], dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms_max, units_all = float(t[0]), float(u[0])
+    value = units_all / (ms_max * 1e-3) / 1e9
+
+    # dominant kernel: the trial-objective projection (K1')
+    peaks, peak_src = load_peaks()
+    k1_ms, k1_n = prof["objective_projection"]
+    samples_per_launch = float(np.mean([active_samples(g, vs) for vs in batches[:3]]))
+    k1_avg_ms = k1_ms / max(k1_n, 1)
+    sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
+    achieved = (OPS_PER_SAMPLE * samples_per_launch / (k1_avg_ms * 1e-3) / 1e12
+                if k1_n else None)
+    roofline = {"kernel": "k1_project (trial objective, Step 2c)", "bound": "alu",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock seen)"
+                               % sm_clock,
+                "ops_per_sample": OPS_PER_SAMPLE, "samples_per_launch": samples_per_launch,
+                "avg_launch_ms": k1_avg_ms}
+    k3_ms, k3_n = prof["prox_reduce"]
+    k3_avg = k3_ms / max(k3_n, 1)
+    k3_gbs = K3_BYTES_PER_VOXEL * g.n_vox / (k3_avg * 1e-3) / 1e9 if k3_n else None
+    kernels = {name: {"ms": round(v[0], 3), "launches": v[1]} for name, v in prof.items()}
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%s: %d^3 volume, %d views, %dx%d detector, mini-batch %d views, "
+                                  "FP32 storage, FP32 accumulation, FP64 line-search sums"
+                                  % (wl.name, g.nx, g.n_views, g.nu, g.nv, wl.N0),
+                      "N_t": stats[0]["N_t"], "alpha0": 1e-3, "beta": 0.5, "mu": wl.mu,
+                      "l2": "inputs larger than L2 (volume %.0f MB, data %.0f MB)"
+                            % (g.n_vox * 4 / 1e6, g.n_views * g.nu * g.nv * 4 / 1e6),
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "backtracks_per_step": statistics.mean(st["backtracks"] for st in stats),
+           "roofline": roofline,
+           "roofline_k3": {"kernel": "k_prox_padded", "bound": "hbm", "achieved": k3_gbs,
+                           "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                           "frac": (k3_gbs / peaks["hbm_gbs"]) if k3_gbs else None,
+                           "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},
+           "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk}
+
+    # end to end through the same C-ABI call with host (pinned) buffers
+    if args.e2e_steps > 0:
+        S2 = fbl.fblisa_create(G, params)
+        xh = torch.zeros(g.vol_shape, dtype=torch.float32).pin_memory()
+        bh = b.cpu().pin_memory()
+        S2.step(xh, bh)
+        torch.cuda.synchronize(device)
+        e0 = time.perf_counter()
+        st2 = [S2.step(xh, bh) for _ in range(args.e2e_steps)]
+        torch.cuda.synchronize(device)
+        e_ms = (time.perf_counter() - e0) * 1e3
+        u2 = sum(step_units(st, g) for st in st2)
+        h2d = g.n_vox * 4 + st2[0]["N_t"] * g.nu * g.nv * 4 + st2[0]["N_t"] * 4
+        d2h = g.n_vox * 4 + 40 * (statistics.mean(s["backtracks"] for s in st2) + 1)
+        out["e2e"] = {"value": u2 / (e_ms * 1e-3) / 1e9 * (units_all / units), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": e_ms / args.e2e_steps}
+        del S2, xh, bh
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, xt)
+    return out
+
+
+def cpu_baseline(wl, xt=None):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+    import numpy as np
+    import oracle
+    import synth
+    g = wl.geom
+    if xt is None:
+        xt = synth.phantom(g, wl.n_ellipsoids, wl.seed_phantom, inclusions=wl.inclusions,
+                           texture_std=wl.texture_std)
+    x64 = np.asarray(xt, dtype=np.float64)
+    rng = np.random.default_rng(1)
+    y = rng.standard_normal((1, g.nv, g.nu))
+    t0 = time.perf_counter()
+    oracle.project(g, x64, [0])
+    t1 = time.perf_counter()
+    oracle.backproject(g, y, [1])
+    t2 = time.perf_counter()
+    units = g.nu * g.nv * g.nx + g.n_vox
+    return {"value": units / (t2 - t0) / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "FP64 oracle: forward projection of 1 view + scatter adjoint of 1 view "
+                      "at the full %d^3 / %dx%d geometry (fwd %.2f s, adjoint %.2f s)"
+                      % (g.nx, g.nu, g.nv, t1 - t0, t2 - t1)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, each step one bounded sample of the workload."""
+    import numpy as np
+    import oracle
+    import synth
+    wl = synth.WORKLOADS[args.workload]
+    g = wl.geom
+    xt = synth.phantom(g, wl.n_ellipsoids, wl.seed_phantom, inclusions=wl.inclusions,
+                       texture_std=wl.texture_std).astype(np.float64)
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal((1, g.nv, g.nu))
+
+    def one(v):
+        oracle.project(g, xt, [v % g.n_views])
+        oracle.backproject(g, y, [(v + 1) % g.n_views])
+
+    for w in range(args.warmup):
+        one(w)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        one(args.warmup + s)
+    sec = time.perf_counter() - t0
+    units = args.steps * (g.nu * g.nv * g.nx + g.n_vox)
+    value = units / sec / 1e9
+    sample = ("each step: FP64 oracle forward projection of 1 view + scatter adjoint of 1 view "
+              "at the full %d^3 / %dx%d geometry" % (g.nx, g.nu, g.nv))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s: %d^3 volume, %d views, %dx%d detector (oracle sample)"
+                                   % (wl.name, g.nx, g.n_views, g.nu, g.nv)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = env_rank()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

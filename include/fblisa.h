@@ -1,0 +1,253 @@
+/*
+ * fblisa.h -- C ABI of the GB300 (sm_103a) FB-LISA hot path.
+ *
+ * FB-LISA solves the CT problem of eq. (2.1),
+ *     argmin_x  1/2 ||A x - b||^2 + mu ||x||_1 + indicator{x >= 0},
+ * with Algorithm 1: mini-batches N_k of whole 2D projections (eq. (2.5)), a
+ * forward-backward step x_bar = prox_{alpha R}(x - alpha grad f_N(x)) and the
+ * sufficient-decrease line search (2.3).  This header exposes the operator
+ * A_N, its exact transpose, the fused objective and prox reductions, and the
+ * solver itself.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Geometry (the paper delegates the discretisation to a library, Sec. 3;
+ * this is the library's own definition):
+ *   view i has angle angles[i] (or 2*pi*i/n_views); source
+ *   s = SOD*(cos, sin, 0); detector centre -(SDD-SOD)*(cos, sin, 0); detector
+ *   axes e_u = (-sin, cos, 0), e_v = (0, 0, 1); pixel (iu, iv) centre
+ *   c + (iu-(nu-1)/2)*du*e_u + (iv-(nv-1)/2)*dv*e_v, one ray per pixel.
+ *   Voxel (i, j, k) centre ((i-(nx-1)/2)*vx, (j-(ny-1)/2)*vy, (k-(nz-1)/2)*vz).
+ *   A is Joseph-type: along the dominant axis a of the ray direction d (ties
+ *   to the lower axis) every voxel plane is crossed once, the crossing is
+ *   interpolated bilinearly with zero outside the volume, and the row weight
+ *   is v_a*|d|/|d_a|.
+ * Layouts: volumes are [nz][ny][nx] (x fastest); sinograms are
+ *   [view][nv][nu] (u fastest).  A call's "views" list selects which views,
+ *   in which order; the k-th listed view fills slice k of a batch sinogram.
+ * Pointers: every volume or sinogram pointer may be device memory (the fast
+ *   path) or host memory (pageable or pinned); host data are staged through
+ *   device buffers on the call's stream.  View lists and scalar outputs are
+ *   always host pointers.  All buffers are owned by the caller.
+ * Streams: "stream" is a cudaStream_t (NULL = the legacy default stream).
+ *   project/backproject enqueue work and return; calls with host outputs
+ *   (scalars or host volumes) return after the results are on the host.
+ * Device: objects are bound to the CUDA device current at creation; calls
+ *   must be made with that device current.
+ * Errors: calls return a status and never throw; the message of the last
+ *   failure on the calling thread is fbl_last_error().  On error no output
+ *   that was passed in is partially updated by a solver step (the trial
+ *   point lives in library scratch until it is accepted).
+ * There is no CPU fallback: without a usable sm_103a device every call that
+ *   computes returns FBL_E_CUDA.
+ */
+#ifndef FBLISA_H
+#define FBLISA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FBL_API __attribute__((visibility("default")))
+#else
+#define FBL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FBL_OK = 0,
+    FBL_E_INVAL = 1,        /* bad argument (null pointer, size, view index, dtype) */
+    FBL_E_NOMEM = 2,        /* device or host allocation failed */
+    FBL_E_CUDA = 3,         /* CUDA runtime error (message has the CUDA error string) */
+    FBL_E_UNSUPPORTED = 4,  /* geometry outside what the kernels handle */
+    FBL_E_LINESEARCH = 5,   /* no step passed (2.3) within max_backtracks */
+    FBL_E_NONFINITE = 6,    /* NaN/Inf in an objective or reduction */
+    FBL_E_TIMEOUT = 7       /* a bounded device wait ran out */
+} fbl_status;
+
+/* Storage types of volumes and sinograms.  Arithmetic is FP32 along rays and
+ * voxel sums, FP64 in the line-search reductions, whatever the storage. */
+typedef enum { FBL_F32 = 0, FBL_BF16 = 1, FBL_F16 = 2 } fbl_dtype;
+
+typedef struct fbl_geometry fbl_geometry; /* opaque, library-owned */
+typedef struct fbl_solver fbl_solver;     /* opaque, library-owned */
+
+/* Circular cone-beam geometry; lengths in mm, angles in radians. */
+typedef struct {
+    int32_t nx, ny, nz;       /* volume size in voxels */
+    double vx, vy, vz;        /* voxel size */
+    int32_t n_views;          /* n_theta, number of views */
+    const double *angles;     /* n_views angles, or NULL for 2*pi*i/n_views (copied) */
+    double sod, sdd;          /* source-origin and source-detector distances */
+    int32_t nu, nv;           /* detector pixels */
+    double du, dv;            /* detector pixel size */
+} fbl_geometry_desc;
+
+/* Hyperparameters of Algorithm 1 (names as in the paper, Sec. 2.2 and Sec. 3). */
+typedef struct {
+    double alpha0;            /* initial step alpha_0 (Sec. 3: 1e-3) */
+    double beta;              /* backtracking factor beta in (0, 1) */
+    double mu;                /* l1 weight mu of eq. (2.1) */
+    double C;                 /* C of Step 1 (Sec. 3: M = 1) */
+    double eps_base;          /* eps_k = eps_base^k (Sec. 3: 0.99) */
+    int32_t N0;               /* initial mini-batch size N_0 (Sec. 3: 8) */
+    int32_t n_max;            /* largest mini-batch, 0 = n_views */
+    int32_t max_backtracks;   /* cap on step reductions per iteration */
+    int32_t proposal;         /* 0: reset alpha to alpha_0 (Step 2d); 1: learned proposal */
+    uint64_t seed;            /* mini-batch permutation seed */
+    int32_t x_dtype;          /* fbl_dtype of the caller's x and the solver's iterates */
+    int32_t b_dtype;          /* fbl_dtype of the caller's b */
+    int32_t use_graph;        /* 1: run each iteration's line search as one CUDA graph */
+    int32_t force_reject;     /* test hook: every trial fails (2.3) */
+} fbl_params;
+
+/* Record of one iteration of Algorithm 1. */
+typedef struct {
+    int64_t k;                /* iteration index (0-based) */
+    int32_t epoch;            /* t (1-based) */
+    int32_t N_t;              /* mini-batch size */
+    int32_t backtracks;       /* step reductions before acceptance */
+    int32_t status;           /* fbl_status of the iteration */
+    double alpha;             /* accepted step alpha_k */
+    double alpha_init;        /* first trial step of the line search */
+    double rho0;              /* ||A_N x - b_N||^2 */
+    double f_x;               /* f_N(x) = n_theta/(2 N_t) rho0, eq. (2.5) */
+    double f_xbar;            /* f_N(x_bar) at the accepted step */
+    double gTd;               /* grad f_N(x)^T (x_bar - x) */
+    double dnorm2;            /* ||x_bar - x||^2 */
+    double margin;            /* rhs of (2.3) minus f_N(x_bar), >= 0 when accepted */
+} fbl_step_stats;
+
+/* Defaults: alpha0 1e-3, beta 0.5, mu 1, C 1, eps_base 0.99, N0 8, n_max 0,
+ * max_backtracks 60, proposal 0, seed 0, F32 storage, no graph, no hook. */
+FBL_API void fbl_params_default(fbl_params *p);
+
+/*
+ * geometry_create -- validate a cone-beam geometry and build its device
+ * tables on the current device.  The geometry is that of A in eq. (2.1),
+ * n = n_p * n_theta rows (Sec. 2.1).
+ * Errors: FBL_E_INVAL for non-positive sizes or distances;
+ * FBL_E_UNSUPPORTED if the volume is not strictly between source and
+ * detector, if a ray is dominated by its z component, or if a padded volume
+ * would exceed 2^31 elements.
+ */
+FBL_API fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometry **out);
+FBL_API void geometry_destroy(fbl_geometry *g);
+
+/*
+ * project -- y = A_N x (eq. (2.5)'s restricted operator) for the n_sel views
+ * listed in views[] (host int32).  x: [nz][ny][nx] of x_dtype; y:
+ * [n_sel][nv][nu] of y_dtype, overwritten.
+ */
+FBL_API fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dtype, const int32_t *views,
+                   int32_t n_sel, void *y, int32_t y_dtype, void *stream);
+
+/*
+ * backproject -- x = A_N^T y (or x += A_N^T y when accumulate != 0), the
+ * exact transpose of project, needed by grad f_N in Step 2b of Algorithm 1.
+ * y: [n_sel][nv][nu] of y_dtype; x: [nz][ny][nx] float32.
+ */
+FBL_API fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_dtype,
+                       const int32_t *views, int32_t n_sel, float *x, int32_t accumulate,
+                       void *stream);
+
+/*
+ * residual_norm -- rho = ||A_N x - b_N||^2 in FP64 (the mini-batch fidelity
+ * of eq. (2.5) up to the factor n_theta/(2 N_t)), without storing A_N x.
+ * b: the full sinogram [n_views][nv][nu] of b_dtype; the listed views are
+ * read from it.  *rho_host is written before the call returns.
+ */
+FBL_API fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_t x_dtype,
+                         const int32_t *views, int32_t n_sel, const void *b, int32_t b_dtype,
+                         double *rho_host, void *stream);
+
+/*
+ * prox_reduce -- the forward-backward point of Step 2c,
+ *   x_bar = prox_{alpha R}(x - alpha g) = max(x - alpha g - alpha mu, 0),
+ * R = mu||.||_1 + indicator{x >= 0} (eq. (2.1)), stored in x_dtype, and the
+ * FP64 reductions the test (2.3) needs, taken over the stored x_bar:
+ *   out3_host[0] = g^T (x_bar - x), out3_host[1] = ||x_bar - x||^2,
+ *   out3_host[2] = ||x_bar||_1.
+ * x, x_bar: n elements of x_dtype (x_bar must not alias x); g: n float32.
+ */
+FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, int64_t n, double alpha,
+                       double mu, void *xbar, double *out3_host, void *stream);
+
+/*
+ * fblisa_create -- a solver for Algorithm 1 on geometry g with the given
+ * hyperparameters; owns its scratch (gradient, trial point, residual,
+ * reduction slots) and its schedule/mini-batch state (Step 1, Step 2a).
+ * The geometry must outlive the solver.
+ */
+FBL_API fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, fbl_solver **out);
+FBL_API void fblisa_destroy(fbl_solver *s);
+
+/*
+ * fblisa_step -- one iteration k of Algorithm 1 (Steps 2a-2d, plus Step 1
+ * and Step 3 at epoch boundaries): draw N_k, compute f_N(x) and grad f_N(x),
+ * backtrack alpha until (2.3) holds, set x <- x_bar.
+ * x: [nz][ny][nx] of x_dtype, updated in place on acceptance; b: full
+ * sinogram [n_views][nv][nu] of b_dtype.  *stats (may be NULL) is filled.
+ * Returns after the iteration's scalars are on the host.  On
+ * FBL_E_LINESEARCH / FBL_E_NONFINITE x is unchanged and the iteration
+ * counter does not advance.
+ */
+FBL_API fbl_status fblisa_step(fbl_solver *s, void *x, const void *b, fbl_step_stats *stats,
+                       void *stream);
+
+/*
+ * fblisa_run -- `epochs` epochs of Algorithm 1 from the solver's current
+ * position.  trace (may be NULL) receives up to trace_cap records;
+ * *n_steps (may be NULL) the number of iterations done.
+ */
+FBL_API fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t epochs,
+                      fbl_step_stats *trace, int64_t trace_cap, int64_t *n_steps, void *stream);
+
+/*
+ * Per-kernel device time of a solver, for performance reporting: with
+ * profiling enabled the solver brackets each of its kernel launches with
+ * CUDA events on the launching stream.  Classes: 0 residual projection
+ * (Step 2b), 1 trial-objective projection (Step 2c), 2 gradient
+ * backprojection, 3 prox + reductions, 4 final FP64 reductions, 5 volume
+ * packing.  Launch counts are kept whether or not timing is enabled.
+ */
+enum { FBL_PROF_CLASSES = 6 };
+typedef struct {
+    double ms[FBL_PROF_CLASSES];        /* summed device time */
+    int64_t launches[FBL_PROF_CLASSES]; /* kernel launches */
+} fbl_profile;
+
+/* Enable (1) or disable (0) event timing; if out is non-NULL, copy the
+ * counters accumulated so far into it and reset them. */
+FBL_API fbl_status fblisa_profile(fbl_solver *s, int32_t enable, fbl_profile *out);
+
+/* The views of the most recent iteration's mini-batch N_k (host copy). */
+FBL_API fbl_status fblisa_last_batch(const fbl_solver *s, int32_t *views, int32_t cap, int32_t *n);
+
+/* Message of the last failed call on this thread ("" if none). */
+FBL_API const char *fbl_last_error(void);
+
+/*
+ * Host-only helpers (no device needed).
+ * fbl_schedule -- Step 1 of Algorithm 1 for t = 1..epochs:
+ *   N_t = min{n_max, max{ceil(C / eps_{k_hat + ceil(n/N_{t-1})}), N_0}},
+ *   eps_k = eps_base^k, N_{t-1} = N_0 at t = 1, iters_t = ceil(n/N_t).
+ * fbl_epoch_batches -- the mini-batches of epoch t (Step 2a): a Fisher-Yates
+ *   permutation of 0..n_theta-1 from SplitMix64 (seed XOR t*0xD1B54A32D192ED03;
+ *   draw i swaps entry i with i + floor(u_i (n-i)), u_i = top 53 bits), cut
+ *   into slices of N_t; a short last slice is padded from the front of the
+ *   permutation.  views_out holds ceil(n_theta/N_t)*N_t entries.
+ */
+FBL_API fbl_status fbl_schedule(int32_t n_theta, int32_t N0, int32_t n_max, double C, double eps_base,
+                        int32_t epochs, int32_t *N_out, int32_t *iters_out);
+FBL_API fbl_status fbl_epoch_batches(uint64_t seed, int32_t epoch, int32_t n_theta, int32_t N_t,
+                             int32_t *views_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBLISA_H */

@@ -1,0 +1,339 @@
+"""Python binding of libfblisa, the GB300 (sm_103a) FB-LISA hot path.
+
+Argument marshalling only: every computation runs in the CUDA kernels behind
+the C ABI declared in include/fblisa.h; the names here are the C names.
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CPU/numpy buffers
+are staged to the device by the library itself.  There is no CPU fallback:
+importing this package fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfblisa.so")
+
+F32, BF16, F16 = 0, 1, 2
+STATUS = {0: "FBL_OK", 1: "FBL_E_INVAL", 2: "FBL_E_NOMEM", 3: "FBL_E_CUDA",
+          4: "FBL_E_UNSUPPORTED", 5: "FBL_E_LINESEARCH", 6: "FBL_E_NONFINITE", 7: "FBL_E_TIMEOUT"}
+
+
+class FblError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class fbl_geometry_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("vx", ctypes.c_double), ("vy", ctypes.c_double), ("vz", ctypes.c_double),
+                ("n_views", ctypes.c_int32), ("angles", ctypes.POINTER(ctypes.c_double)),
+                ("sod", ctypes.c_double), ("sdd", ctypes.c_double),
+                ("nu", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("du", ctypes.c_double), ("dv", ctypes.c_double)]
+
+
+class fbl_params(ctypes.Structure):
+    _fields_ = [("alpha0", ctypes.c_double), ("beta", ctypes.c_double), ("mu", ctypes.c_double),
+                ("C", ctypes.c_double), ("eps_base", ctypes.c_double),
+                ("N0", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("max_backtracks", ctypes.c_int32), ("proposal", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("x_dtype", ctypes.c_int32),
+                ("b_dtype", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("force_reject", ctypes.c_int32)]
+
+
+class fbl_step_stats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("epoch", ctypes.c_int32), ("N_t", ctypes.c_int32),
+                ("backtracks", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("alpha_init", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("f_x", ctypes.c_double),
+                ("f_xbar", ctypes.c_double), ("gTd", ctypes.c_double),
+                ("dnorm2", ctypes.c_double), ("margin", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class fbl_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
+
+
+PROFILE_CLASSES = ("residual_projection", "objective_projection", "gradient_backprojection",
+                   "prox_reduce", "final_reduce", "pack")
+
+EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_destroy", "project", "backproject",
+           "residual_norm", "prox_reduce", "fblisa_create", "fblisa_destroy", "fblisa_step",
+           "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
+           "fbl_epoch_batches"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfblisa.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_2605_12085_gb300.build" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, vp, i32, i64, dbl = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "fbl_params_default": (None, [P(fbl_params)]),
+        "geometry_create": (st, [P(fbl_geometry_desc), P(vp)]),
+        "geometry_destroy": (None, [vp]),
+        "project": (st, [vp, vp, i32, P(i32), i32, vp, i32, vp]),
+        "backproject": (st, [vp, vp, i32, P(i32), i32, vp, i32, vp]),
+        "residual_norm": (st, [vp, vp, i32, P(i32), i32, vp, i32, P(dbl), vp]),
+        "prox_reduce": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
+        "fblisa_create": (st, [vp, P(fbl_params), P(vp)]),
+        "fblisa_destroy": (None, [vp]),
+        "fblisa_step": (st, [vp, vp, vp, P(fbl_step_stats), vp]),
+        "fblisa_run": (st, [vp, vp, vp, i32, P(fbl_step_stats), i64, P(i64), vp]),
+        "fblisa_last_batch": (st, [vp, P(i32), i32, P(i32)]),
+        "fblisa_profile": (st, [vp, i32, P(fbl_profile)]),
+        "fbl_last_error": (ctypes.c_char_p, []),
+        "fbl_schedule": (st, [i32, i32, i32, dbl, dbl, i32, P(i32), P(i32)]),
+        "fbl_epoch_batches": (st, [ctypes.c_uint64, i32, i32, i32, P(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != 0:
+        raise FblError(status, lib.fbl_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# Buffers: torch tensors (any device) or numpy arrays
+# ---------------------------------------------------------------------------
+def _dtype_code(a) -> int:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            m = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+            if a.dtype not in m:
+                raise TypeError("unsupported dtype %s" % a.dtype)
+            return m[a.dtype]
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.asarray(a)
+    m = {np.dtype(np.float32): F32, np.dtype(np.float16): F16}
+    if a.dtype not in m:
+        raise TypeError("unsupported dtype %s" % a.dtype)
+    return m[a.dtype]
+
+
+def _ptr(a) -> int:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    if not (isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be a C-contiguous numpy array")
+    return a.ctypes.data
+
+
+def _stream(*arrays, stream=None) -> Optional[int]:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        for a in arrays:
+            if isinstance(a, torch.Tensor) and a.is_cuda:
+                return torch.cuda.current_stream(a.device).cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
+def _views(views) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(list(views), dtype=np.int32))
+
+
+def _like(template, shape, dtype_code):
+    try:
+        import torch
+        if isinstance(template, torch.Tensor):
+            td = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[dtype_code]
+            return torch.empty(shape, dtype=td, device=template.device)
+    except ImportError:  # pragma: no cover
+        pass
+    if dtype_code == BF16:
+        raise TypeError("numpy has no bfloat16: pass torch tensors")
+    return np.empty(shape, dtype=np.float32 if dtype_code == F32 else np.float16)
+
+
+# ---------------------------------------------------------------------------
+# API
+# ---------------------------------------------------------------------------
+class Geometry:
+    """Handle of a fbl_geometry (cone-beam geometry + device tables)."""
+
+    def __init__(self, desc):
+        self.desc = desc
+        self._angles = None
+        d = fbl_geometry_desc()
+        for f in ("nx", "ny", "nz", "vx", "vy", "vz", "n_views", "sod", "sdd", "nu", "nv", "du", "dv"):
+            setattr(d, f, getattr(desc, f))
+        ang = getattr(desc, "angles", None)
+        if ang is not None:
+            self._angles = np.ascontiguousarray(np.asarray(ang, dtype=np.float64))
+            d.angles = self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._c = d
+        h = ctypes.c_void_p()
+        _check(lib.geometry_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.geometry_destroy(h)
+            self.handle = None
+
+    @property
+    def vol_shape(self):
+        return (self.desc.nz, self.desc.ny, self.desc.nx)
+
+    @property
+    def n_views(self):
+        return self.desc.n_views
+
+
+def geometry_create(desc) -> Geometry:
+    return Geometry(desc)
+
+
+def project(geom: Geometry, x, views: Sequence[int], y=None, y_dtype: Optional[int] = None,
+            stream=None):
+    v = _views(views)
+    xd = _dtype_code(x)
+    if y is None:
+        y = _like(x, (v.size, geom.desc.nv, geom.desc.nu), F32 if y_dtype is None else y_dtype)
+    _check(lib.project(geom.handle, _ptr(x), xd, v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                       v.size, _ptr(y), _dtype_code(y), _stream(x, y, stream=stream)))
+    return y
+
+
+def backproject(geom: Geometry, y, views: Sequence[int], x=None, accumulate: bool = False,
+                stream=None):
+    v = _views(views)
+    if x is None:
+        x = _like(y, geom.vol_shape, F32)
+    if _dtype_code(x) != F32:
+        raise TypeError("backproject output must be float32")
+    _check(lib.backproject(geom.handle, _ptr(y), _dtype_code(y),
+                           v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), v.size, _ptr(x),
+                           int(bool(accumulate)), _stream(x, y, stream=stream)))
+    return x
+
+
+def residual_norm(geom: Geometry, x, views: Sequence[int], b, stream=None) -> float:
+    v = _views(views)
+    rho = ctypes.c_double()
+    _check(lib.residual_norm(geom.handle, _ptr(x), _dtype_code(x),
+                             v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), v.size, _ptr(b),
+                             _dtype_code(b), ctypes.byref(rho), _stream(x, b, stream=stream)))
+    return rho.value
+
+
+def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):
+    n = int(np.prod(tuple(x.shape)))
+    if xbar is None:
+        xbar = _like(x, tuple(x.shape), _dtype_code(x))
+    out = (ctypes.c_double * 3)()
+    _check(lib.prox_reduce(_ptr(x), _dtype_code(x), _ptr(g), n, float(alpha), float(mu),
+                           _ptr(xbar), out, _stream(x, g, xbar, stream=stream)))
+    return xbar, (out[0], out[1], out[2])
+
+
+def params_default(**kw) -> fbl_params:
+    p = fbl_params()
+    lib.fbl_params_default(ctypes.byref(p))
+    for k, val in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, val)
+    return p
+
+
+class Solver:
+    """Handle of a fbl_solver (Algorithm 1 state and scratch)."""
+
+    def __init__(self, geom: Geometry, params: fbl_params):
+        self.geom = geom
+        self.params = params
+        h = ctypes.c_void_p()
+        _check(lib.fblisa_create(geom.handle, ctypes.byref(params), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fblisa_destroy(h)
+            self.handle = None
+
+    def step(self, x, b, stream=None) -> dict:
+        st = fbl_step_stats()
+        _check(lib.fblisa_step(self.handle, _ptr(x), _ptr(b), ctypes.byref(st),
+                               _stream(x, b, stream=stream)))
+        return st.as_dict()
+
+    def step_raw(self, x, b, stream=None):
+        """Like step() but returns (status, stats) instead of raising."""
+        st = fbl_step_stats()
+        rc = lib.fblisa_step(self.handle, _ptr(x), _ptr(b), ctypes.byref(st),
+                             _stream(x, b, stream=stream))
+        return rc, st.as_dict()
+
+    def run(self, x, b, epochs: int, trace_cap: int = 100000, stream=None):
+        trace = (fbl_step_stats * max(1, trace_cap))()
+        n = ctypes.c_int64()
+        _check(lib.fblisa_run(self.handle, _ptr(x), _ptr(b), int(epochs), trace, trace_cap,
+                              ctypes.byref(n), _stream(x, b, stream=stream)))
+        return [trace[q].as_dict() for q in range(min(n.value, trace_cap))]
+
+    def profile(self, enable: bool = True):
+        """Return {class: (ms, launches)} accumulated so far (then reset) and
+        switch event timing on or off."""
+        pr = fbl_profile()
+        _check(lib.fblisa_profile(self.handle, int(bool(enable)), ctypes.byref(pr)))
+        return {name: (pr.ms[c], pr.launches[c]) for c, name in enumerate(PROFILE_CLASSES)}
+
+    def last_batch(self):
+        n = ctypes.c_int32()
+        _check(lib.fblisa_last_batch(self.handle, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * max(1, n.value))()
+        _check(lib.fblisa_last_batch(self.handle, buf, n.value, ctypes.byref(n)))
+        return list(buf[:n.value])
+
+
+def fblisa_create(geom: Geometry, params: fbl_params) -> Solver:
+    return Solver(geom, params)
+
+
+def fbl_schedule(n_theta, N0, n_max, C, eps_base, epochs):
+    N = (ctypes.c_int32 * max(1, epochs))()
+    it = (ctypes.c_int32 * max(1, epochs))()
+    _check(lib.fbl_schedule(n_theta, N0, n_max, C, eps_base, epochs, N, it))
+    return [(N[t], it[t]) for t in range(epochs)]
+
+
+def fbl_epoch_batches(seed, epoch, n_theta, N_t):
+    iters = -(-n_theta // N_t)
+    out = (ctypes.c_int32 * (iters * N_t))()
+    _check(lib.fbl_epoch_batches(seed, epoch, n_theta, N_t, out))
+    flat = list(out)
+    return [flat[q * N_t:(q + 1) * N_t] for q in range(iters)]

@@ -1,0 +1,1020 @@
+// C ABI of the FB-LISA hot path: argument checking, geometry tables, the
+// mini-batch schedule and sampling (Algorithm 1, Steps 1 and 2a), the
+// line-search driver (Steps 2b-2d) and the stateless operator calls.  Every
+// numeric step runs in the kernels of k_project.cu, k_backproject.cu and
+// k_prox.cu; this file only prepares tables, moves data and makes the (2.3)
+// decision on four FP64 scalars.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fbl_internal.cuh"
+
+using namespace fbl;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_last_error;
+
+fbl_status fail(fbl_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+fbl_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(FBL_E_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FBL_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool valid_dtype(int dt) { return dt == FBL_F32 || dt == FBL_BF16 || dt == FBL_F16; }
+
+// True when p is device (or managed) memory of the current context.
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+fbl_status check_device(int want) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != want)
+        return fail(FBL_E_INVAL, "object was created on device %d but device %d is current", want,
+                    cur);
+    return FBL_OK;
+}
+
+// Stream-ordered scratch that is released when it goes out of scope.
+struct AsyncBuf {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    AsyncBuf() = default;
+    AsyncBuf(const AsyncBuf &) = delete;
+    AsyncBuf &operator=(const AsyncBuf &) = delete;
+    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+        st = s;
+        return cudaMallocAsync(&p, bytes ? bytes : 16, s);
+    }
+    ~AsyncBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+struct fbl_geometry {
+    fbl_geometry_desc desc;
+    std::vector<double> angles;
+    int device = -1;
+    DevGeom dg;
+    float4 *d_colA = nullptr;
+    float4 *d_colB = nullptr;
+    float2 *d_trig = nullptr;
+};
+
+namespace {
+
+PadLayout layout_for(const fbl_geometry *g, int fam, int dtype) {
+    const fbl_geometry_desc &d = g->desc;
+    return fam ? make_layout(d.ny, d.nx, d.nz, dtype_size(dtype))
+               : make_layout(d.nx, d.ny, d.nz, dtype_size(dtype));
+}
+
+double view_angle(const fbl_geometry_desc &d, const std::vector<double> &ang, int v) {
+    return ang.empty() ? 2.0 * M_PI * (double)v / (double)d.n_views : ang[v];
+}
+
+}  // namespace
+
+extern "C" void fbl_params_default(fbl_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->alpha0 = 1e-3;
+    p->beta = 0.5;
+    p->mu = 1.0;
+    p->C = 1.0;
+    p->eps_base = 0.99;
+    p->N0 = 8;
+    p->n_max = 0;
+    p->max_backtracks = 60;
+    p->proposal = 0;
+    p->seed = 0;
+    p->x_dtype = FBL_F32;
+    p->b_dtype = FBL_F32;
+    p->use_graph = 0;
+    p->force_reject = 0;
+}
+
+extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometry **out) {
+    if (!desc || !out) return fail(FBL_E_INVAL, "geometry_create: null argument");
+    *out = nullptr;
+    const fbl_geometry_desc &d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nu < 1 || d.nv < 1 || d.n_views < 1)
+        return fail(FBL_E_INVAL, "geometry_create: sizes must be positive");
+    if (!(d.vx > 0 && d.vy > 0 && d.vz > 0 && d.du > 0 && d.dv > 0 && d.sod > 0 && d.sdd > d.sod))
+        return fail(FBL_E_INVAL, "geometry_create: need positive voxel/pixel sizes and 0 < SOD < SDD");
+    const double rxy = 0.5 * std::sqrt((d.nx * d.vx) * (d.nx * d.vx) + (d.ny * d.vy) * (d.ny * d.vy));
+    const double slack = std::max(d.vx, d.vy);
+    if (!(rxy + slack < d.sod && rxy + slack < d.sdd - d.sod))
+        return fail(FBL_E_UNSUPPORTED,
+                    "geometry_create: the volume must lie strictly between source and detector");
+    for (int fam = 0; fam < 2; ++fam)
+        for (int es : {2, 4}) {
+            PadLayout L = fam ? make_layout(d.ny, d.nx, d.nz, es) : make_layout(d.nx, d.ny, d.nz, es);
+            if (L.elems() >= (int64_t(1) << 31))
+                return fail(FBL_E_UNSUPPORTED, "geometry_create: volume too large for 32-bit indexing");
+        }
+    auto g = new fbl_geometry();
+    g->desc = d;
+    if (d.angles) {
+        g->angles.assign(d.angles, d.angles + d.n_views);
+        for (double a : g->angles)
+            if (!std::isfinite(a)) {
+                delete g;
+                return fail(FBL_E_INVAL, "geometry_create: non-finite angle");
+            }
+    }
+    g->desc.angles = nullptr;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "geometry_create: no CUDA device");
+    }
+
+    const double cu = 0.5 * (d.nu - 1), cv = 0.5 * (d.nv - 1);
+    const double cxyz[3] = {0.5 * (d.nx - 1), 0.5 * (d.ny - 1), 0.5 * (d.nz - 1)};
+    const double V[3] = {d.vx, d.vy, d.vz};
+    const int Nn[3] = {d.nx, d.ny, d.nz};
+    const double wmax = std::max(std::fabs(0.0 - cv), std::fabs(d.nv - 1 - cv)) * d.dv;
+    const size_t ncol = (size_t)d.n_views * d.nu;
+    std::vector<float4> colA(ncol), colB(ncol);
+    std::vector<float2> trig(d.n_views);
+    double hw = 0.0;
+    for (int v = 0; v < d.n_views; ++v) {
+        const double th = view_angle(d, g->angles, v);
+        const double c = std::cos(th), sn = std::sin(th);
+        trig[v] = make_float2((float)c, (float)sn);
+        const double s[2] = {d.sod * c, d.sod * sn};
+        std::vector<double> qb_first(d.nu), qb_last(d.nu);
+        std::vector<int> famv(d.nu);
+        for (int iu = 0; iu < d.nu; ++iu) {
+            // d = P - s with P = c_det + u e_u, written in the definition's order so
+            // that an exact tie |d_x| == |d_y| is decided like the definition says.
+            const double u = (iu - cu) * d.du;
+            const double off = d.sdd - d.sod;
+            const double Px = -off * c - u * sn, Py = -off * sn + u * c;
+            const double dxy[2] = {Px - s[0], Py - s[1]};
+            const int fam = (std::fabs(dxy[1]) > std::fabs(dxy[0])) ? 1 : 0;
+            const int a = fam, b = 1 - fam;
+            if (wmax > std::fabs(dxy[a])) {
+                delete g;
+                return fail(FBL_E_UNSUPPORTED,
+                            "geometry_create: view %d column %d has rays dominated by z", v, iu);
+            }
+            const double da = dxy[a], db = dxy[b];
+            const double plane0 = -cxyz[a] * V[a] - s[a];  // A_0 - s_a
+            const double qb1 = V[a] * db / (da * V[b]);
+            const double qb0 = (s[b] + plane0 * db / da) / V[b] + cxyz[b];
+            const double zc1 = V[a] / (da * V[2]);
+            const double zc0 = plane0 / (da * V[2]);
+            const double wa = V[a] / std::fabs(da);
+            const double h2 = dxy[0] * dxy[0] + dxy[1] * dxy[1];
+            colA[(size_t)v * d.nu + iu] = make_float4((float)qb0, (float)qb1, (float)zc0, (float)zc1);
+            colB[(size_t)v * d.nu + iu] = make_float4((float)wa, (float)h2, (float)fam, 0.f);
+            qb_first[iu] = qb0;
+            qb_last[iu] = qb0 + (Nn[a] - 1) * qb1;
+            famv[iu] = fam;
+        }
+        for (int iu = 0; iu + 1 < d.nu; ++iu) {
+            if (famv[iu] != famv[iu + 1]) continue;
+            const double d0 = std::fabs(qb_first[iu + 1] - qb_first[iu]);
+            const double d1 = std::fabs(qb_last[iu + 1] - qb_last[iu]);
+            const double dm = std::min(d0, d1);
+            if (dm > 0) hw = std::max(hw, 1.0 / dm);
+        }
+    }
+    if (hw == 0.0) hw = (double)d.nu;  // a single column: take every column as a candidate
+    hw = hw * 1.02 + 0.05;
+
+    DevGeom &dg = g->dg;
+    dg.nx = d.nx;
+    dg.ny = d.ny;
+    dg.nz = d.nz;
+    dg.nu = d.nu;
+    dg.nv = d.nv;
+    dg.n_views = d.n_views;
+    dg.cu = (float)cu;
+    dg.cv = (float)cv;
+    dg.du = (float)d.du;
+    dg.dv = (float)d.dv;
+    dg.cx = (float)cxyz[0];
+    dg.cy = (float)cxyz[1];
+    dg.cz = (float)cxyz[2];
+    dg.vx = (float)d.vx;
+    dg.vy = (float)d.vy;
+    dg.vz = (float)d.vz;
+    dg.sod = (float)d.sod;
+    dg.sdd = (float)d.sdd;
+    dg.inv_du = (float)(1.0 / d.du);
+    dg.hwu = (float)hw;
+
+    e = cudaMalloc(&g->d_colA, ncol * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_colB, ncol * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_trig, d.n_views * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_colA, colA.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_colB, colB.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_trig, trig.data(), d.n_views * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        geometry_destroy(g);
+        return cuda_fail(e, "geometry_create: device tables");
+    }
+    dg.colA = g->d_colA;
+    dg.colB = g->d_colB;
+    dg.trig = g->d_trig;
+    *out = g;
+    return FBL_OK;
+}
+
+extern "C" void geometry_destroy(fbl_geometry *g) {
+    if (!g) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (g->device >= 0 && cur != g->device) cudaSetDevice(g->device);
+    cudaFree(g->d_colA);
+    cudaFree(g->d_colB);
+    cudaFree(g->d_trig);
+    if (g->device >= 0 && cur >= 0 && cur != g->device) cudaSetDevice(cur);
+    delete g;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers: Step 1 schedule and Step 2a sampling
+// ---------------------------------------------------------------------------
+namespace {
+
+const uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+const uint64_t kEpochKey = 0xD1B54A32D192ED03ull;
+
+// SplitMix64 output function (Steele, Lea & Flood, 2014; "variant 13" mixer).
+uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void permutation(uint64_t seed, int32_t epoch, int32_t n, std::vector<int32_t> &perm) {
+    const uint64_t state = seed ^ ((uint64_t)(int64_t)epoch * kEpochKey);
+    perm.resize(n);
+    for (int32_t i = 0; i < n; ++i) perm[i] = i;
+    for (int32_t i = 0; i + 1 < n; ++i) {
+        const uint64_t z = sm64_mix(state + (uint64_t)(i + 1) * kGamma);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        int32_t j = i + (int32_t)std::floor(u * (double)(n - i));
+        if (j > n - 1) j = n - 1;
+        std::swap(perm[i], perm[j]);
+    }
+}
+
+void batches(uint64_t seed, int32_t epoch, int32_t n, int32_t N_t, std::vector<int32_t> &out) {
+    std::vector<int32_t> perm;
+    permutation(seed, epoch, n, perm);
+    const int32_t iters = (n + N_t - 1) / N_t;
+    out.assign((size_t)iters * N_t, 0);
+    for (int32_t it = 0; it < iters; ++it)
+        for (int32_t q = 0; q < N_t; ++q) {
+            const int32_t pos = it * N_t + q;
+            out[pos] = pos < n ? perm[pos] : perm[pos - n];
+        }
+}
+
+int32_t next_batch_size(int32_t n_theta, int32_t N0, int32_t n_max, double C, double eps_base,
+                        int64_t k_hat, int32_t N_prev) {
+    const int64_t K = k_hat + (n_theta + N_prev - 1) / N_prev;
+    const double q = std::ceil(C / std::pow(eps_base, (double)K));
+    int64_t N = q > 2e9 ? (int64_t)2e9 : (int64_t)q;
+    if (N < N0) N = N0;
+    if (N > n_max) N = n_max;
+    return (int32_t)N;
+}
+
+}  // namespace
+
+extern "C" fbl_status fbl_schedule(int32_t n_theta, int32_t N0, int32_t n_max, double C,
+                                   double eps_base, int32_t epochs, int32_t *N_out,
+                                   int32_t *iters_out) {
+    if (n_theta < 1 || N0 < 1 || N0 > n_theta || epochs < 0 || !(C > 0) ||
+        !(eps_base > 0 && eps_base < 1) || (epochs > 0 && (!N_out || !iters_out)))
+        return fail(FBL_E_INVAL, "fbl_schedule: bad argument");
+    if (n_max <= 0) n_max = n_theta;
+    if (n_max < N0 || n_max > n_theta) return fail(FBL_E_INVAL, "fbl_schedule: need N0 <= n_max <= n_theta");
+    int64_t k_hat = 0;
+    int32_t N_prev = N0;
+    for (int32_t t = 0; t < epochs; ++t) {
+        const int32_t N = next_batch_size(n_theta, N0, n_max, C, eps_base, k_hat, N_prev);
+        N_out[t] = N;
+        iters_out[t] = (n_theta + N - 1) / N;
+        k_hat += iters_out[t];
+        N_prev = N;
+    }
+    return FBL_OK;
+}
+
+extern "C" fbl_status fbl_epoch_batches(uint64_t seed, int32_t epoch, int32_t n_theta, int32_t N_t,
+                                        int32_t *views_out) {
+    if (n_theta < 1 || N_t < 1 || N_t > n_theta || !views_out)
+        return fail(FBL_E_INVAL, "fbl_epoch_batches: bad argument");
+    std::vector<int32_t> out;
+    batches(seed, epoch, n_theta, N_t, out);
+    std::memcpy(views_out, out.data(), out.size() * sizeof(int32_t));
+    return FBL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stateless operator calls
+// ---------------------------------------------------------------------------
+namespace {
+
+fbl_status check_views(const fbl_geometry *g, const int32_t *views, int32_t n_sel) {
+    if (n_sel < 0) return fail(FBL_E_INVAL, "negative view count");
+    if (n_sel > 0 && !views) return fail(FBL_E_INVAL, "null view list");
+    if (n_sel > 65535) return fail(FBL_E_INVAL, "at most 65535 views per call");
+    for (int32_t q = 0; q < n_sel; ++q)
+        if (views[q] < 0 || views[q] >= g->desc.n_views)
+            return fail(FBL_E_INVAL, "view index %d out of range [0, %d)", views[q], g->desc.n_views);
+    return FBL_OK;
+}
+
+// Device copy of a host view list.
+fbl_status upload_views(const int32_t *views, int32_t n, AsyncBuf &buf, cudaStream_t st) {
+    CK(buf.alloc((size_t)n * sizeof(int32_t), st), "view list");
+    if (n) CK(cudaMemcpyAsync(buf.p, views, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+              "view list copy");
+    return FBL_OK;
+}
+
+// Device pointer for a caller buffer: itself if on the device, else a staged copy.
+fbl_status device_input(const void *p, size_t bytes, AsyncBuf &stage, const void **dev,
+                        cudaStream_t st) {
+    if (is_device_ptr(p)) {
+        *dev = p;
+        return FBL_OK;
+    }
+    CK(stage.alloc(bytes, st), "input staging");
+    CK(cudaMemcpyAsync(stage.p, p, bytes, cudaMemcpyHostToDevice, st), "input H2D");
+    *dev = stage.p;
+    return FBL_OK;
+}
+
+// Padded copies of a caller volume (both layouts), stream-ordered.
+fbl_status pack_volume(const fbl_geometry *g, const void *xdev, int dtype, AsyncBuf &pY,
+                       AsyncBuf &pX, PadLayout &LY, PadLayout &LX, cudaStream_t st) {
+    LY = layout_for(g, 1, dtype);
+    LX = layout_for(g, 0, dtype);
+    const int es = dtype_size(dtype);
+    CK(pY.alloc((size_t)LY.elems() * es, st), "padded volume");
+    CK(pX.alloc((size_t)LX.elems() * es, st), "padded volume");
+    CK(cudaMemsetAsync(pY.p, 0, (size_t)LY.elems() * es, st), "memset");
+    CK(cudaMemsetAsync(pX.p, 0, (size_t)LX.elems() * es, st), "memset");
+    CK(launch_pack(xdev, dtype, g->desc.nx, g->desc.ny, g->desc.nz, pY.p, LY, pX.p, LX, st), "pack");
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dtype,
+                              const int32_t *views, int32_t n_sel, void *y, int32_t y_dtype,
+                              void *stream) {
+    if (!g || !x || !y) return fail(FBL_E_INVAL, "project: null argument");
+    if (!valid_dtype(x_dtype) || !valid_dtype(y_dtype)) return fail(FBL_E_INVAL, "project: bad dtype");
+    fbl_status st = check_views(g, views, n_sel);
+    if (st) return st;
+    if ((st = check_device(g->device))) return st;
+    if (n_sel == 0) return FBL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fbl_geometry_desc &d = g->desc;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    const size_t ny_out = (size_t)n_sel * d.nv * d.nu;
+    AsyncBuf dviews, xs, pY, pX, ys;
+    if ((st = upload_views(views, n_sel, dviews, s))) return st;
+    const void *xd = nullptr;
+    if ((st = device_input(x, nvox * dtype_size(x_dtype), xs, &xd, s))) return st;
+    PadLayout LY, LX;
+    if ((st = pack_volume(g, xd, x_dtype, pY, pX, LY, LX, s))) return st;
+    const bool y_dev = is_device_ptr(y);
+    void *yd = y;
+    if (!y_dev) {
+        CK(ys.alloc(ny_out * dtype_size(y_dtype), s), "output staging");
+        yd = ys.p;
+    }
+    CK(launch_project(PROJ_STORE, g->dg, pX.p, LX, pY.p, LY, x_dtype, (const int32_t *)dviews.p,
+                      n_sel, nullptr, FBL_F32, nullptr, yd, y_dtype, nullptr, nullptr, s),
+       "project kernel");
+    if (!y_dev) {
+        CK(cudaMemcpyAsync(y, yd, ny_out * dtype_size(y_dtype), cudaMemcpyDeviceToHost, s), "output D2H");
+        CK(cudaStreamSynchronize(s), "project");
+    }
+    return FBL_OK;
+}
+
+extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_dtype,
+                                  const int32_t *views, int32_t n_sel, float *x,
+                                  int32_t accumulate, void *stream) {
+    if (!g || !y || !x) return fail(FBL_E_INVAL, "backproject: null argument");
+    if (!valid_dtype(y_dtype)) return fail(FBL_E_INVAL, "backproject: bad dtype");
+    fbl_status st = check_views(g, views, n_sel);
+    if (st) return st;
+    if ((st = check_device(g->device))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fbl_geometry_desc &d = g->desc;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    const size_t ny_in = (size_t)n_sel * d.nv * d.nu;
+    const bool x_dev = is_device_ptr(x);
+    AsyncBuf dviews, ys, rt, xs;
+    float *xd = x;
+    if (!x_dev) {
+        CK(xs.alloc(nvox * sizeof(float), s), "output staging");
+        xd = (float *)xs.p;
+        if (accumulate) CK(cudaMemcpyAsync(xd, x, nvox * sizeof(float), cudaMemcpyHostToDevice, s), "x H2D");
+    }
+    if (n_sel == 0) {
+        if (!accumulate) CK(cudaMemsetAsync(xd, 0, nvox * sizeof(float), s), "memset");
+    } else {
+        if ((st = upload_views(views, n_sel, dviews, s))) return st;
+        const void *yd = nullptr;
+        if ((st = device_input(y, ny_in * dtype_size(y_dtype), ys, &yd, s))) return st;
+        CK(rt.alloc(ny_in * sizeof(float), s), "weighted sinogram");
+        CK(launch_weight(g->dg, yd, y_dtype, (const int32_t *)dviews.p, n_sel, (float *)rt.p, s),
+           "weight kernel");
+        CK(launch_backproject(g->dg, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f, xd,
+                              accumulate, s),
+           "backproject kernel");
+    }
+    if (!x_dev) {
+        CK(cudaMemcpyAsync(x, xd, nvox * sizeof(float), cudaMemcpyDeviceToHost, s), "x D2H");
+        CK(cudaStreamSynchronize(s), "backproject");
+    }
+    return FBL_OK;
+}
+
+namespace {
+
+// The listed views of b gathered into a batch on the device (b on the host),
+// or b itself with a device view map (b on the device).
+fbl_status batch_data(const fbl_geometry *g, const void *b, int b_dtype, const int32_t *views_h,
+                      const int32_t *views_d, int32_t n_sel, AsyncBuf &stage, const void **bd,
+                      const int32_t **bmap, cudaStream_t s) {
+    const fbl_geometry_desc &d = g->desc;
+    const size_t per_view = (size_t)d.nv * d.nu * dtype_size(b_dtype);
+    if (is_device_ptr(b)) {
+        *bd = b;
+        *bmap = views_d;
+        return FBL_OK;
+    }
+    CK(stage.alloc(per_view * n_sel, s), "data staging");
+    for (int32_t q = 0; q < n_sel; ++q)
+        CK(cudaMemcpyAsync((char *)stage.p + per_view * q, (const char *)b + per_view * views_h[q],
+                           per_view, cudaMemcpyHostToDevice, s),
+           "data H2D");
+    *bd = stage.p;
+    *bmap = nullptr;
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_t x_dtype,
+                                    const int32_t *views, int32_t n_sel, const void *b,
+                                    int32_t b_dtype, double *rho_host, void *stream) {
+    if (!g || !x || !b || !rho_host) return fail(FBL_E_INVAL, "residual_norm: null argument");
+    if (!valid_dtype(x_dtype) || !valid_dtype(b_dtype)) return fail(FBL_E_INVAL, "residual_norm: bad dtype");
+    fbl_status st = check_views(g, views, n_sel);
+    if (st) return st;
+    if ((st = check_device(g->device))) return st;
+    if (n_sel == 0) {
+        *rho_host = 0.0;
+        return FBL_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const fbl_geometry_desc &d = g->desc;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    AsyncBuf dviews, xs, pY, pX, bs, part, res;
+    if ((st = upload_views(views, n_sel, dviews, s))) return st;
+    const void *xd = nullptr;
+    if ((st = device_input(x, nvox * dtype_size(x_dtype), xs, &xd, s))) return st;
+    PadLayout LY, LX;
+    if ((st = pack_volume(g, xd, x_dtype, pY, pX, LY, LX, s))) return st;
+    const void *bd = nullptr;
+    const int32_t *bmap = nullptr;
+    if ((st = batch_data(g, b, b_dtype, views, (const int32_t *)dviews.p, n_sel, bs, &bd, &bmap, s)))
+        return st;
+    const int np = project_num_partials(g->dg, n_sel);
+    CK(part.alloc((size_t)np * sizeof(double), s), "partials");
+    CK(res.alloc(sizeof(double), s), "result");
+    CK(launch_project(PROJ_NORM, g->dg, pX.p, LX, pY.p, LY, x_dtype, (const int32_t *)dviews.p, n_sel,
+                      bd, b_dtype, bmap, nullptr, FBL_F32, (double *)part.p, nullptr, s),
+       "objective kernel");
+    CK(launch_reduce((const double *)part.p, np, np, 1, (double *)res.p, s), "reduce");
+    CK(cudaMemcpyAsync(rho_host, res.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    CK(cudaStreamSynchronize(s), "residual_norm");
+    if (!std::isfinite(*rho_host)) return fail(FBL_E_NONFINITE, "residual_norm: non-finite result");
+    return FBL_OK;
+}
+
+extern "C" fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *gr, int64_t n,
+                                  double alpha, double mu, void *xbar, double *out3_host,
+                                  void *stream) {
+    if (!x || !gr || !xbar || !out3_host) return fail(FBL_E_INVAL, "prox_reduce: null argument");
+    if (!valid_dtype(x_dtype)) return fail(FBL_E_INVAL, "prox_reduce: bad dtype");
+    if (n < 0) return fail(FBL_E_INVAL, "prox_reduce: negative size");
+    if (x == xbar) return fail(FBL_E_INVAL, "prox_reduce: x_bar must not alias x");
+    if (!(alpha > 0) || !std::isfinite(alpha) || !std::isfinite(mu))
+        return fail(FBL_E_INVAL, "prox_reduce: need alpha > 0 and finite mu");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = dtype_size(x_dtype);
+    AsyncBuf xs, gs, xbs, part, res;
+    const void *xd = nullptr;
+    const void *gd = nullptr;
+    fbl_status st;
+    if ((st = device_input(x, (size_t)n * es, xs, &xd, s))) return st;
+    if ((st = device_input(gr, (size_t)n * sizeof(float), gs, &gd, s))) return st;
+    const bool xb_dev = is_device_ptr(xbar);
+    void *xbd = xbar;
+    if (!xb_dev) {
+        CK(xbs.alloc((size_t)n * es, s), "output staging");
+        xbd = xbs.p;
+    }
+    const int np = prox_flat_num_partials(n);
+    CK(part.alloc((size_t)np * 3 * sizeof(double), s), "partials");
+    CK(res.alloc(3 * sizeof(double), s), "result");
+    CK(launch_prox_flat(xd, (const float *)gd, n, (float)alpha, (float)(alpha * mu), xbd, x_dtype,
+                        (double *)part.p, nullptr, s),
+       "prox kernel");
+    CK(launch_reduce((const double *)part.p, np, np, 3, (double *)res.p, s), "reduce");
+    CK(cudaMemcpyAsync(out3_host, res.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    if (!xb_dev) CK(cudaMemcpyAsync(xbar, xbd, (size_t)n * es, cudaMemcpyDeviceToHost, s), "x_bar D2H");
+    CK(cudaStreamSynchronize(s), "prox_reduce");
+    return FBL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solver: Algorithm 1
+// ---------------------------------------------------------------------------
+struct fbl_solver {
+    const fbl_geometry *g = nullptr;
+    fbl_params p;
+    int device = -1;
+    int32_t n_max = 0;
+    // schedule / sampling state
+    int32_t epoch = 0;            // t of the current epoch (0: none started)
+    int32_t N_t = 0, N_prev = 0;
+    int32_t iters_epoch = 0, iter_in_epoch = 0;
+    int64_t k = 0, k_hat = 0;
+    std::vector<int32_t> epoch_views;
+    std::vector<int32_t> last_batch;
+    // device state
+    PadLayout LY, LX;
+    size_t padY_bytes = 0, padX_bytes = 0;
+    void *stY = nullptr, *stX = nullptr, *trY = nullptr, *trX = nullptr;
+    float *grad = nullptr;
+    float *rt = nullptr;
+    size_t rt_cap = 0;
+    void *bstage = nullptr;
+    size_t bstage_cap = 0;
+    void *xstage = nullptr;
+    int32_t *d_views = nullptr;
+    int32_t *h_views = nullptr;   // pinned
+    double *partials = nullptr;
+    size_t partials_cap = 0;
+    double *d_sc = nullptr;       // [8] device scalars
+    double *h_sc = nullptr;       // [8] pinned
+    // profiling: launch counts always, CUDA-event times when enabled
+    bool prof_on = false;
+    double prof_ms[FBL_PROF_CLASSES] = {};
+    int64_t prof_launches[FBL_PROF_CLASSES] = {};
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+namespace {
+
+void solver_free(fbl_solver *s) {
+    cudaFree(s->stY);
+    cudaFree(s->stX);
+    cudaFree(s->trY);
+    cudaFree(s->trX);
+    cudaFree(s->grad);
+    cudaFree(s->rt);
+    cudaFree(s->bstage);
+    cudaFree(s->xstage);
+    cudaFree(s->d_views);
+    cudaFree(s->partials);
+    cudaFree(s->d_sc);
+    cudaFreeHost(s->h_views);
+    cudaFreeHost(s->h_sc);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    s->ev_pool.clear();
+}
+
+cudaEvent_t prof_event(fbl_solver *s) {
+    if (s->ev_next == s->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        s->ev_pool.push_back(e);
+    }
+    return s->ev_pool[s->ev_next++];
+}
+
+// Launch a kernel of class cls, counted, and bracketed by events when profiling.
+template <class F>
+cudaError_t prof_launch(fbl_solver *s, int cls, cudaStream_t st, F &&launch) {
+    s->prof_launches[cls] += 1;
+    if (!s->prof_on) return launch();
+    cudaEvent_t a = prof_event(s), b = prof_event(s);
+    if (!a || !b) return launch();
+    cudaEventRecord(a, st);
+    cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    s->ev_pending.push_back({cls, {a, b}});
+    return e;
+}
+
+// After a stream synchronisation: fold the completed event pairs into the totals.
+void prof_flush(fbl_solver *s) {
+    for (auto &pe : s->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess)
+            s->prof_ms[pe.first] += ms;
+    }
+    s->ev_pending.clear();
+    s->ev_next = 0;
+}
+
+fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
+    const fbl_geometry_desc &d = s->g->desc;
+    const size_t need = (size_t)N * d.nv * d.nu;
+    if (need > s->rt_cap) {
+        cudaFree(s->rt);
+        s->rt = nullptr;
+        s->rt_cap = 0;
+        CK(cudaMalloc(&s->rt, need * sizeof(float)), "residual buffer");
+        s->rt_cap = need;
+    }
+    const size_t np = std::max((size_t)project_num_partials(s->g->dg, N),
+                               (size_t)3 * prox_padded_num_partials(d.nx, d.ny, d.nz));
+    if (np > s->partials_cap) {
+        cudaFree(s->partials);
+        s->partials = nullptr;
+        s->partials_cap = 0;
+        CK(cudaMalloc(&s->partials, np * sizeof(double)), "partials");
+        s->partials_cap = np;
+    }
+    return FBL_OK;
+}
+
+// Step 1 (and Step 3 for the epoch just finished) when an epoch ends.
+void begin_epoch_if_needed(fbl_solver *s) {
+    if (s->epoch > 0 && s->iter_in_epoch < s->iters_epoch) return;
+    const fbl_geometry_desc &d = s->g->desc;
+    if (s->epoch > 0) s->k_hat = s->k;
+    const int32_t prev = s->epoch > 0 ? s->N_t : s->p.N0;
+    s->N_t = next_batch_size(d.n_views, s->p.N0, s->n_max, s->p.C, s->p.eps_base, s->k_hat, prev);
+    s->N_prev = prev;
+    s->epoch += 1;
+    s->iters_epoch = (d.n_views + s->N_t - 1) / s->N_t;
+    s->iter_in_epoch = 0;
+    batches(s->p.seed, s->epoch, d.n_views, s->N_t, s->epoch_views);
+}
+
+// One iteration of Algorithm 1 on the solver's padded state (stY/stX).
+fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_stats *stats,
+                          cudaStream_t st) {
+    const fbl_geometry *g = s->g;
+    const fbl_geometry_desc &d = g->desc;
+    // Remember the schedule position so that a failed iteration leaves it unchanged.
+    const int32_t save_epoch = s->epoch, save_N = s->N_t, save_Np = s->N_prev;
+    const int32_t save_iters = s->iters_epoch, save_it = s->iter_in_epoch;
+    const int64_t save_khat = s->k_hat;
+    std::vector<int32_t> save_views;
+    const bool new_epoch = !(s->epoch > 0 && s->iter_in_epoch < s->iters_epoch);
+    if (new_epoch) save_views = s->epoch_views;
+    begin_epoch_if_needed(s);
+    auto restore = [&]() {
+        s->epoch = save_epoch;
+        s->N_t = save_N;
+        s->N_prev = save_Np;
+        s->iters_epoch = save_iters;
+        s->iter_in_epoch = save_it;
+        s->k_hat = save_khat;
+        if (new_epoch) s->epoch_views = save_views;
+    };
+    const int32_t N = s->N_t;
+    fbl_status rc = ensure_batch_buffers(s, N);
+    if (rc) {
+        restore();
+        return rc;
+    }
+    const int32_t *views = s->epoch_views.data() + (size_t)s->iter_in_epoch * N;
+    std::memcpy(s->h_views, views, N * sizeof(int32_t));
+    s->last_batch.assign(views, views + N);
+    CK(cudaMemcpyAsync(s->d_views, s->h_views, N * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+       "view list");
+    const void *bd = b;
+    const int32_t *bmap = s->d_views;
+    if (!b_dev) {
+        const size_t per_view = (size_t)d.nv * d.nu * dtype_size(s->p.b_dtype);
+        if (per_view * N > s->bstage_cap) {
+            cudaFree(s->bstage);
+            s->bstage = nullptr;
+            s->bstage_cap = 0;
+            cudaError_t e = cudaMalloc(&s->bstage, per_view * N);
+            if (e != cudaSuccess) {
+                restore();
+                return cuda_fail(e, "data staging");
+            }
+            s->bstage_cap = per_view * N;
+        }
+        for (int32_t q = 0; q < N; ++q)
+            CK(cudaMemcpyAsync((char *)s->bstage + per_view * q, (const char *)b + per_view * views[q],
+                               per_view, cudaMemcpyHostToDevice, st),
+               "data H2D");
+        bd = s->bstage;
+        bmap = nullptr;
+    }
+    const int xdt = s->p.x_dtype;
+    const double scale = (double)d.n_views / (double)N;
+    // Step 2b: residual, f_N(x), grad f_N(x)
+    int np = 0;
+    CK(prof_launch(s, 0, st, [&] {
+           return launch_project(PROJ_RESID, g->dg, s->stX, s->LX, s->stY, s->LY, xdt, s->d_views, N,
+                                 bd, s->p.b_dtype, bmap, s->rt, FBL_F32, s->partials, &np, st);
+       }),
+       "residual kernel");
+    CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
+       "reduce");
+    CK(prof_launch(s, 2, st, [&] {
+           return launch_backproject(g->dg, s->rt, s->d_views, N, (float)scale, s->grad, 0, st);
+       }),
+       "gradient kernel");
+    // Step 2c: backtracking on (2.3)
+    double alpha = s->p.alpha0;
+    const double alpha_init = alpha;
+    const int64_t nvox = (int64_t)d.nx * d.ny * d.nz;
+    (void)nvox;
+    bool accepted = false;
+    int bt = 0;
+    double rho0 = 0, rho1 = 0, gTd = 0, dd = 0, f_x = 0, f_xb = 0, rhs = 0;
+    for (bt = 0; bt <= s->p.max_backtracks; ++bt) {
+        int npp = 0;
+        CK(prof_launch(s, 3, st, [&] {
+               return launch_prox_padded(s->stY, s->LY, s->grad, (float)alpha, (float)(alpha * s->p.mu),
+                                         s->trY, s->trX, s->LX, xdt, d.nx, d.ny, d.nz, s->partials,
+                                         &npp, st);
+           }),
+           "prox kernel");
+        CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
+           "reduce");
+        CK(prof_launch(s, 1, st, [&] {
+               return launch_project(PROJ_NORM, g->dg, s->trX, s->LX, s->trY, s->LY, xdt, s->d_views, N,
+                                     bd, s->p.b_dtype, bmap, nullptr, FBL_F32, s->partials, &np, st);
+           }),
+           "objective kernel");
+        CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 4, st); }),
+           "reduce");
+        CK(cudaMemcpyAsync(s->h_sc, s->d_sc, 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+        CK(cudaStreamSynchronize(st), "line search");
+        prof_flush(s);
+        rho0 = s->h_sc[0];
+        gTd = s->h_sc[1];
+        dd = s->h_sc[2];
+        rho1 = s->h_sc[4];
+        f_x = 0.5 * scale * rho0;
+        f_xb = 0.5 * scale * rho1;
+        rhs = f_x + gTd + dd / (2.0 * alpha);
+        if (!std::isfinite(f_x) || !std::isfinite(f_xb) || !std::isfinite(rhs)) {
+            restore();
+            return fail(FBL_E_NONFINITE, "fblisa_step: non-finite objective or reduction at k=%lld",
+                        (long long)s->k);
+        }
+        if (!s->p.force_reject && f_xb <= rhs) {
+            accepted = true;
+            break;
+        }
+        alpha *= s->p.beta;
+    }
+    if (stats) {
+        stats->k = s->k;
+        stats->epoch = s->epoch;
+        stats->N_t = N;
+        stats->backtracks = accepted ? bt : s->p.max_backtracks;
+        stats->alpha = accepted ? alpha : alpha / s->p.beta;
+        stats->alpha_init = alpha_init;
+        stats->rho0 = rho0;
+        stats->f_x = f_x;
+        stats->f_xbar = f_xb;
+        stats->gTd = gTd;
+        stats->dnorm2 = dd;
+        stats->margin = rhs - f_xb;
+        stats->status = accepted ? FBL_OK : FBL_E_LINESEARCH;
+    }
+    if (!accepted) {
+        restore();
+        return fail(FBL_E_LINESEARCH, "fblisa_step: no step passed (2.3) within %d backtracks",
+                    s->p.max_backtracks);
+    }
+    // Step 2d: x <- x_bar (swap the padded buffers); alpha restarts from alpha_0.
+    std::swap(s->stY, s->trY);
+    std::swap(s->stX, s->trX);
+    s->k += 1;
+    s->iter_in_epoch += 1;
+    return FBL_OK;
+}
+
+fbl_status solver_load_x(fbl_solver *s, const void *x, bool x_dev, cudaStream_t st) {
+    const fbl_geometry_desc &d = s->g->desc;
+    const size_t bytes = (size_t)d.nx * d.ny * d.nz * dtype_size(s->p.x_dtype);
+    const void *src = x;
+    if (!x_dev) {
+        CK(cudaMemcpyAsync(s->xstage, x, bytes, cudaMemcpyHostToDevice, st), "x H2D");
+        src = s->xstage;
+    }
+    CK(prof_launch(s, 5, st, [&] {
+           return launch_pack(src, s->p.x_dtype, d.nx, d.ny, d.nz, s->stY, s->LY, s->stX, s->LX, st);
+       }),
+       "pack");
+    return FBL_OK;
+}
+
+fbl_status solver_store_x(fbl_solver *s, void *x, bool x_dev, cudaStream_t st) {
+    const fbl_geometry_desc &d = s->g->desc;
+    const int es = dtype_size(s->p.x_dtype);
+    const size_t bytes = (size_t)d.nx * d.ny * d.nz * es;
+    if (x_dev) {
+        CK(copy_unpad(s->stY, s->LY, es, x, d.nx, d.ny, d.nz, st), "x copy");
+    } else {
+        CK(copy_unpad(s->stY, s->LY, es, s->xstage, d.nx, d.ny, d.nz, st), "x copy");
+        CK(cudaMemcpyAsync(x, s->xstage, bytes, cudaMemcpyDeviceToHost, st), "x D2H");
+    }
+    CK(cudaStreamSynchronize(st), "x store");
+    prof_flush(s);
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, fbl_solver **out) {
+    if (!g || !p || !out) return fail(FBL_E_INVAL, "fblisa_create: null argument");
+    *out = nullptr;
+    fbl_status st = check_device(g->device);
+    if (st) return st;
+    const fbl_geometry_desc &d = g->desc;
+    if (!valid_dtype(p->x_dtype) || !valid_dtype(p->b_dtype)) return fail(FBL_E_INVAL, "fblisa_create: bad dtype");
+    if (!(p->alpha0 > 0) || !(p->beta > 0 && p->beta < 1) || !(p->mu >= 0) || !(p->C > 0) ||
+        !(p->eps_base > 0 && p->eps_base < 1) || p->max_backtracks < 0)
+        return fail(FBL_E_INVAL, "fblisa_create: need alpha0 > 0, 0 < beta < 1, mu >= 0, C > 0, 0 < eps_base < 1");
+    const int32_t n_max = p->n_max > 0 ? p->n_max : d.n_views;
+    if (p->N0 < 1 || p->N0 > n_max || n_max > d.n_views)
+        return fail(FBL_E_INVAL, "fblisa_create: need 1 <= N0 <= n_max <= n_views");
+    if (p->proposal != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: learned proposal not available");
+    if (p->use_graph != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: graph mode not available");
+    auto s = new fbl_solver();
+    s->g = g;
+    s->p = *p;
+    s->device = g->device;
+    s->n_max = n_max;
+    s->LY = layout_for(g, 1, p->x_dtype);
+    s->LX = layout_for(g, 0, p->x_dtype);
+    const int es = dtype_size(p->x_dtype);
+    s->padY_bytes = (size_t)s->LY.elems() * es;
+    s->padX_bytes = (size_t)s->LX.elems() * es;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    cudaError_t e = cudaSuccess;
+    void **pads[4] = {&s->stY, &s->trY, &s->stX, &s->trX};
+    const size_t padb[4] = {s->padY_bytes, s->padY_bytes, s->padX_bytes, s->padX_bytes};
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+        e = cudaMalloc(pads[q], padb[q]);
+        if (e == cudaSuccess) e = cudaMemset(*pads[q], 0, padb[q]);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->grad, nvox * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->xstage, nvox * es);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_views, (size_t)d.n_views * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_views, (size_t)d.n_views * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_sc, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        solver_free(s);
+        delete s;
+        return cuda_fail(e, "fblisa_create");
+    }
+    *out = s;
+    return FBL_OK;
+}
+
+extern "C" void fblisa_destroy(fbl_solver *s) {
+    if (!s) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    solver_free(s);
+    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);
+    delete s;
+}
+
+extern "C" fbl_status fblisa_step(fbl_solver *s, void *x, const void *b, fbl_step_stats *stats,
+                                  void *stream) {
+    if (!s || !x || !b) return fail(FBL_E_INVAL, "fblisa_step: null argument");
+    fbl_status st = check_device(s->device);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const bool x_dev = is_device_ptr(x), b_dev = is_device_ptr(b);
+    if ((st = solver_load_x(s, x, x_dev, cs))) return st;
+    if ((st = solver_iterate(s, b, b_dev, stats, cs))) return st;
+    return solver_store_x(s, x, x_dev, cs);
+}
+
+extern "C" fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t epochs,
+                                 fbl_step_stats *trace, int64_t trace_cap, int64_t *n_steps,
+                                 void *stream) {
+    if (!s || !x || !b) return fail(FBL_E_INVAL, "fblisa_run: null argument");
+    if (epochs < 0 || trace_cap < 0) return fail(FBL_E_INVAL, "fblisa_run: negative count");
+    fbl_status st = check_device(s->device);
+    if (st) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const bool x_dev = is_device_ptr(x), b_dev = is_device_ptr(b);
+    if (n_steps) *n_steps = 0;
+    if ((st = solver_load_x(s, x, x_dev, cs))) return st;
+    const int32_t target = s->epoch + epochs - ((s->epoch > 0 && s->iter_in_epoch < s->iters_epoch) ? 1 : 0);
+    int64_t done = 0;
+    fbl_status rc = FBL_OK;
+    while (true) {
+        const bool epoch_open = s->epoch > 0 && s->iter_in_epoch < s->iters_epoch;
+        if (!epoch_open && s->epoch >= target) break;
+        fbl_step_stats rec;
+        rc = solver_iterate(s, b, b_dev, &rec, cs);
+        if (trace && done < trace_cap) trace[done] = rec;
+        if (rc) break;
+        ++done;
+    }
+    if (n_steps) *n_steps = done;
+    std::string keep = g_last_error;
+    fbl_status st2 = solver_store_x(s, x, x_dev, cs);
+    if (rc) {
+        g_last_error = keep;
+        return rc;
+    }
+    return st2;
+}
+
+extern "C" fbl_status fblisa_profile(fbl_solver *s, int32_t enable, fbl_profile *out) {
+    if (!s) return fail(FBL_E_INVAL, "fblisa_profile: null solver");
+    if (out) {
+        for (int c = 0; c < FBL_PROF_CLASSES; ++c) {
+            out->ms[c] = s->prof_ms[c];
+            out->launches[c] = s->prof_launches[c];
+            s->prof_ms[c] = 0.0;
+            s->prof_launches[c] = 0;
+        }
+    }
+    s->prof_on = enable != 0;
+    return FBL_OK;
+}
+
+extern "C" fbl_status fblisa_last_batch(const fbl_solver *s, int32_t *views, int32_t cap, int32_t *n) {
+    if (!s || !n) return fail(FBL_E_INVAL, "fblisa_last_batch: null argument");
+    *n = (int32_t)s->last_batch.size();
+    if (views) {
+        if (cap < *n) return fail(FBL_E_INVAL, "fblisa_last_batch: buffer too small");
+        std::memcpy(views, s->last_batch.data(), s->last_batch.size() * sizeof(int32_t));
+    }
+    return FBL_OK;
+}
+
+extern "C" const char *fbl_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,141 @@
+// Internal declarations shared by the C-ABI layer and the sm_103a kernels of
+// the FB-LISA hot path.  Nothing here is exported.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fblisa.h"
+
+namespace fbl {
+
+// ---------------------------------------------------------------------------
+// Storage types.  Arithmetic is always FP32 (FP64 for the line-search sums).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int dtype_size(int dt) { return dt == FBL_F32 ? 4 : 2; }
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// Read-only load through the non-coherent path, converted to FP32.
+template <typename T> __device__ __forceinline__ float ldg_f32(const T *p) { return to_f32(__ldg(p)); }
+
+// ---------------------------------------------------------------------------
+// Padded volume layouts used by the projector.
+//
+// A ray of family f crosses the planes m of its dominant axis a (a = x for
+// f = 0, a = y for f = 1); in-plane it moves along the other horizontal axis
+// b and along z.  Family f reads a copy of the volume laid out as
+//     P_f[k + 1][m][b + PL]      (k in [-1, nz], m in [0, Na), b in [-PL, pitch-PL))
+// with zeros outside the volume, so the bilinear footprint of any crossing
+// with -1 < q_b < Nb and -1 < q_z < nz reads in bounds and sees zero padding
+// without a branch.  PL = 16 bytes of elements keeps the interior of every
+// row 16-byte aligned; pitch is a multiple of PL with at least one zero after
+// the last element.
+// ---------------------------------------------------------------------------
+struct PadLayout {
+    int Na, Nb, nz;
+    int PL;      // left pad, elements
+    int pitch;   // row pitch, elements
+    __host__ __device__ int64_t elems() const { return (int64_t)(nz + 2) * Na * pitch; }
+    __host__ __device__ int64_t index(int b, int m, int k) const {
+        return ((int64_t)(k + 1) * Na + m) * pitch + b + PL;
+    }
+};
+
+inline PadLayout make_layout(int Na, int Nb, int nz, int esize) {
+    PadLayout L;
+    L.Na = Na;
+    L.Nb = Nb;
+    L.nz = nz;
+    L.PL = 16 / esize;
+    int need = L.PL + Nb + 1;
+    L.pitch = (need + L.PL - 1) / L.PL * L.PL;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry tables on the device.
+//
+// For view v and detector column iu (all rays of a column share the
+// horizontal direction because e_v is vertical) the host computes in FP64:
+//   fam   family: 0 if |d_x| >= |d_y| (x-planes), else 1 (y-planes)
+//   qb0, qb1  q_b(m) = qb0 + m*qb1, continuous in-plane index at plane m
+//   zc0, zc1  Zc(m) = zc0 + m*zc1 = t(m)/vz, so q_z = w*Zc(m) + cz with
+//             w = (iv - cv)*dv the vertical pixel offset
+//   wa, h2    row weight v_a*|d|/|d_a| = wa*sqrt(h2 + w^2)
+// ---------------------------------------------------------------------------
+struct DevGeom {
+    int nx, ny, nz, nu, nv, n_views;
+    float cu, cv, du, dv;        // detector centre (index units) and pixel size
+    float cx, cy, cz;            // volume centre in index units
+    float vx, vy, vz;            // voxel size
+    float sod, sdd, inv_du;
+    float hwu;                   // half width, in columns, of a voxel's column footprint
+    const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1)
+    const float4 *colB;          // [n_views][nu] (wa, h2, fam, 0)
+    const float2 *trig;          // [n_views] (cos, sin)
+};
+
+enum ProjMode { PROJ_STORE = 0, PROJ_RESID = 1, PROJ_NORM = 2 };
+
+// Kernel launchers (each returns the launch error, if any).
+cudaError_t launch_pack(const void *x, int x_dtype, int nx, int ny, int nz, void *padY,
+                        PadLayout LY, void *padX, PadLayout LX, cudaStream_t st);
+
+// mode STORE: out[s] = A_{views[s]} x  (out_dtype)
+// mode RESID: out[s] = W * (A x - b[bview(s)]) as float32, partials += r^2
+// mode NORM:  partials += (A x - b)^2 only
+// b_views: device list mapping slot s to the view index inside b (NULL: b is
+// already the batch, slot s at index s).
+cudaError_t launch_project(int mode, const DevGeom &g, const void *padX, PadLayout LX,
+                           const void *padY, PadLayout LY, int x_dtype, const int32_t *views,
+                           int n_sel, const void *b, int b_dtype, const int32_t *b_views,
+                           void *out, int out_dtype, double *partials, int *n_partials,
+                           cudaStream_t st);
+int project_num_partials(const DevGeom &g, int n_sel);
+
+// rt[s][iv][iu] = W(ray) * y[s][iv][iu] (the row weight folded in for K2)
+cudaError_t launch_weight(const DevGeom &g, const void *y, int y_dtype, const int32_t *views,
+                          int n_sel, float *rt, cudaStream_t st);
+
+// g[k][j][i] = scale * sum over listed views of the transpose taps of rt
+// (+= when accumulate).
+cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
+                               int n_sel, float scale, float *gout, int accumulate,
+                               cudaStream_t st);
+
+// x_bar = max(x - alpha*gr - alpha*mu, 0) for the solver's padded state:
+// reads padY (current x), gr (natural layout), writes trialY / trialX;
+// partials[3][nblk] = (g^T d, d^T d, |x_bar|_1) per block.
+cudaError_t launch_prox_padded(const void *padY, PadLayout LY, const float *gr, float alpha,
+                               float amu, void *trialY, void *trialX, PadLayout LX, int dtype,
+                               int nx, int ny, int nz, double *partials, int *n_partials,
+                               cudaStream_t st);
+int prox_padded_num_partials(int nx, int ny, int nz);
+
+// Flat prox on n elements (public prox_reduce).
+cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float alpha, float amu,
+                             void *xbar, int dtype, double *partials, int *n_partials,
+                             cudaStream_t st);
+int prox_flat_num_partials(int64_t n);
+
+// out[c] = sum of partials[c*stride + 0 .. n) in a fixed order, for c < ncomp.
+cudaError_t launch_reduce(const double *partials, int n, int stride, int ncomp, double *out,
+                          cudaStream_t st);
+
+// Copy the interior of a padded Y-layout volume to a natural [nz][ny][nx] one.
+cudaError_t copy_unpad(const void *padY, PadLayout LY, int esize, void *x, int nx, int ny, int nz,
+                       cudaStream_t st);
+
+}  // namespace fbl

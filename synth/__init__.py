@@ -191,14 +191,29 @@ def _box_blur(f: np.ndarray, radius: int) -> np.ndarray:
     return f
 
 
+def _texture(shape, seed: int, std: float, cell: int = 4) -> np.ndarray:
+    """Smooth low-amplitude texture: a seeded N(0,1) field on a grid `cell`
+    times coarser, box-blurred twice with radius 1, repeated up to the full
+    grid and scaled to standard deviation `std`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    coarse = tuple(-(-n // cell) for n in shape)
+    t = rng.standard_normal(coarse, dtype=np.float32)
+    for _ in range(2):
+        t = _box_blur(t, 1).astype(np.float32)
+    for ax in range(3):
+        t = np.repeat(t, cell, axis=ax)
+    t = np.ascontiguousarray(t[:shape[0], :shape[1], :shape[2]])
+    t *= np.float32(std / max(float(t.std()), 1e-30))
+    return t
+
+
 def phantom(geom: Geometry, n_ellipsoids: int, seed: int, inclusions: int = 0,
             texture_std: float = 0.0, dtype=np.float32) -> np.ndarray:
     """Point-sampled ellipsoid phantom [nz][ny][nx], clipped to [0, 1].
 
     The value of a voxel is the sum of the additive ellipsoids that contain
     its centre; "set" inclusions then overwrite with 1.0; an optional texture
-    (seeded N(0,1) field, box-blurred three times with radius 2, scaled to
-    ``texture_std``) is added inside the background ellipsoid; finally the
+    (see _texture) is added inside the background ellipsoid; finally the
     volume is clipped to [0, 1].  Each ellipsoid is evaluated in float64 over
     its bounding box only.
     """
@@ -233,12 +248,7 @@ def phantom(geom: Geometry, n_ellipsoids: int, seed: int, inclusions: int = 0,
                     bg_mask = np.zeros(geom.vol_shape, dtype=bool)
                 bg_mask[sl] |= inside
     if texture_std > 0.0 and bg_mask is not None:
-        rng = np.random.Generator(np.random.PCG64(seed + 777))
-        tex = rng.standard_normal(geom.vol_shape, dtype=np.float32)
-        for _ in range(3):
-            tex = _box_blur(tex, 2).astype(np.float32)
-        tex *= np.float32(texture_std / max(float(tex.std()), 1e-30))
-        vol += np.where(bg_mask, tex, np.float32(0.0))
+        vol += np.where(bg_mask, _texture(geom.vol_shape, seed + 777, texture_std), np.float32(0.0))
     np.clip(vol, 0.0, 1.0, out=vol)
     return vol.astype(dtype, copy=False)
 
