@@ -140,7 +140,7 @@ FBL_API void geometry_destroy(fbl_geometry *g);
 /*
  * project -- y = A_N x (eq. (2.5)'s restricted operator) for the n_sel views
  * listed in views[] (host int32).  x: [nz][ny][nx] of x_dtype; y:
- * [n_sel][nv][nu] of y_dtype, overwritten.
+ * [n_sel][nv][nu] of y_dtype, overwritten (may be NULL when n_sel == 0).
  */
 FBL_API fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dtype, const int32_t *views,
                    int32_t n_sel, void *y, int32_t y_dtype, void *stream);
@@ -148,7 +148,8 @@ FBL_API fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dtype
 /*
  * backproject -- x = A_N^T y (or x += A_N^T y when accumulate != 0), the
  * exact transpose of project, needed by grad f_N in Step 2b of Algorithm 1.
- * y: [n_sel][nv][nu] of y_dtype; x: [nz][ny][nx] float32.
+ * y: [n_sel][nv][nu] of y_dtype (may be NULL when n_sel == 0); x: [nz][ny][nx]
+ * float32 (zeroed when n_sel == 0 and accumulate == 0).
  */
 FBL_API fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_dtype,
                        const int32_t *views, int32_t n_sel, float *x, int32_t accumulate,

@@ -96,6 +96,7 @@ struct fbl_geometry {
     DevGeom dg;
     float4 *d_colA = nullptr;
     float4 *d_colB = nullptr;
+    FxCol *d_colF = nullptr;
     float2 *d_trig = nullptr;
 };
 
@@ -175,6 +176,8 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     const double wmax = std::max(std::fabs(0.0 - cv), std::fabs(d.nv - 1 - cv)) * d.dv;
     const size_t ncol = (size_t)d.n_views * d.nu;
     std::vector<float4> colA(ncol), colB(ncol);
+    std::vector<FxCol> colF(ncol);
+    auto fx = [](double v) { return (long long)std::llround(v * FX_ONE); };
     std::vector<float2> trig(d.n_views);
     double hw = 0.0;
     for (int v = 0; v < d.n_views; ++v) {
@@ -207,6 +210,7 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
             const double wa = V[a] / std::fabs(da);
             const double h2 = dxy[0] * dxy[0] + dxy[1] * dxy[1];
             colA[(size_t)v * d.nu + iu] = make_float4((float)qb0, (float)qb1, (float)zc0, (float)zc1);
+            colF[(size_t)v * d.nu + iu] = FxCol{fx(qb0), fx(qb1), fx(0.5 * d.dv * zc0), fx(0.5 * d.dv * zc1)};
             colB[(size_t)v * d.nu + iu] = make_float4((float)wa, (float)h2, (float)fam, 0.f);
             qb_first[iu] = qb0;
             qb_last[iu] = qb0 + (Nn[a] - 1) * qb1;
@@ -244,10 +248,13 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     dg.sdd = (float)d.sdd;
     dg.inv_du = (float)(1.0 / d.du);
     dg.hwu = (float)hw;
+    dg.cz_fx = (long long)std::llround(cxyz[2] * FX_ONE);
 
     e = cudaMalloc(&g->d_colA, ncol * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colB, ncol * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_trig, d.n_views * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_colF, ncol * sizeof(FxCol));
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_colF, colF.data(), ncol * sizeof(FxCol), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_colA, colA.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_colB, colB.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_trig, trig.data(), d.n_views * sizeof(float2), cudaMemcpyHostToDevice);
@@ -256,6 +263,7 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
         return cuda_fail(e, "geometry_create: device tables");
     }
     dg.colA = g->d_colA;
+    dg.colF = g->d_colF;
     dg.colB = g->d_colB;
     dg.trig = g->d_trig;
     *out = g;
@@ -270,6 +278,7 @@ extern "C" void geometry_destroy(fbl_geometry *g) {
     cudaFree(g->d_colA);
     cudaFree(g->d_colB);
     cudaFree(g->d_trig);
+    cudaFree(g->d_colF);
     if (g->device >= 0 && cur >= 0 && cur != g->device) cudaSetDevice(cur);
     delete g;
 }
@@ -411,7 +420,7 @@ fbl_status pack_volume(const fbl_geometry *g, const void *xdev, int dtype, Async
 extern "C" fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dtype,
                               const int32_t *views, int32_t n_sel, void *y, int32_t y_dtype,
                               void *stream) {
-    if (!g || !x || !y) return fail(FBL_E_INVAL, "project: null argument");
+    if (!g || !x || (n_sel > 0 && !y)) return fail(FBL_E_INVAL, "project: null argument");
     if (!valid_dtype(x_dtype) || !valid_dtype(y_dtype)) return fail(FBL_E_INVAL, "project: bad dtype");
     fbl_status st = check_views(g, views, n_sel);
     if (st) return st;
@@ -446,7 +455,7 @@ extern "C" fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dt
 extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_dtype,
                                   const int32_t *views, int32_t n_sel, float *x,
                                   int32_t accumulate, void *stream) {
-    if (!g || !y || !x) return fail(FBL_E_INVAL, "backproject: null argument");
+    if (!g || !x || (n_sel > 0 && !y)) return fail(FBL_E_INVAL, "backproject: null argument");
     if (!valid_dtype(y_dtype)) return fail(FBL_E_INVAL, "backproject: bad dtype");
     fbl_status st = check_views(g, views, n_sel);
     if (st) return st;
@@ -512,7 +521,8 @@ fbl_status batch_data(const fbl_geometry *g, const void *b, int b_dtype, const i
 extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_t x_dtype,
                                     const int32_t *views, int32_t n_sel, const void *b,
                                     int32_t b_dtype, double *rho_host, void *stream) {
-    if (!g || !x || !b || !rho_host) return fail(FBL_E_INVAL, "residual_norm: null argument");
+    if (!g || !x || (n_sel > 0 && !b) || !rho_host)
+        return fail(FBL_E_INVAL, "residual_norm: null argument");
     if (!valid_dtype(x_dtype) || !valid_dtype(b_dtype)) return fail(FBL_E_INVAL, "residual_norm: bad dtype");
     fbl_status st = check_views(g, views, n_sel);
     if (st) return st;

@@ -75,6 +75,28 @@ inline PadLayout make_layout(int Na, int Nb, int nz, int esize) {
 //             w = (iv - cv)*dv the vertical pixel offset
 //   wa, h2    row weight v_a*|d|/|d_a| = wa*sqrt(h2 + w^2)
 // ---------------------------------------------------------------------------
+// Crossing positions are exact fixed-point numbers with FX_BITS fractional
+// bits held in int64 (Q.40): stepping from plane to plane adds an integer, so
+// every crossing equals its closed form exactly, K1 and K2 compute identical
+// positions, and the bilinear weights carry full FP32 precision whatever the
+// volume size (an FP32 coordinate near 512 would only resolve 3e-5 voxel).
+constexpr int FX_BITS = 40;
+constexpr double FX_ONE = 1099511627776.0;  // 2^40
+
+__host__ __device__ __forceinline__ int fx_floor(long long q) { return (int)(q >> FX_BITS); }
+// Fractional part in [0, 1) to 23 bits, as an FP32 number.
+__device__ __forceinline__ float fx_frac(long long q) {
+    const unsigned bits = (unsigned)((unsigned long long)q >> (FX_BITS - 23)) & 0x7FFFFFu;
+    return __uint_as_float(bits | 0x3F800000u) - 1.0f;
+}
+
+// Fixed-point column constants: q_b(m) = qb0 + m*qb1 and, for the detector
+// row iv with n = 2*iv - (nv-1) (so that w = n*dv/2),
+// q_z(m) = n*(h0 + m*h1) + cz, all in Q.40.
+struct FxCol {
+    long long qb0, qb1, h0, h1;
+};
+
 struct DevGeom {
     int nx, ny, nz, nu, nv, n_views;
     float cu, cv, du, dv;        // detector centre (index units) and pixel size
@@ -82,7 +104,9 @@ struct DevGeom {
     float vx, vy, vz;            // voxel size
     float sod, sdd, inv_du;
     float hwu;                   // half width, in columns, of a voxel's column footprint
-    const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1)
+    long long cz_fx;             // cz in Q.40
+    const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
+    const FxCol *colF;           // [n_views][nu] exact fixed-point constants
     const float4 *colB;          // [n_views][nu] (wa, h2, fam, 0)
     const float2 *trig;          // [n_views] (cos, sin)
 };

@@ -5,11 +5,13 @@
 // A ray of family f touches voxel (i, j, k) only on the plane m of its
 // dominant axis that contains the voxel (m = i for x-planes, m = j for
 // y-planes), with weight wb * wz: wb from the in-plane crossing q_b(m) of its
-// column and wz from the vertical crossing q_z(m).  The gather enumerates
+// column and wz from the vertical crossing q_z(m).  Both crossings are the
+// exact Q.40 fixed-point numbers K1 steps through, so the two kernels use the
+// same weights bit for bit.  The gather enumerates
 //   * the detector columns iu within hwu of the voxel centre's projection
 //     (a geometry-wide bound on the footprint, computed on the host), and for
-//     each its family, plane m and in-plane weight wb, computed with exactly
-//     K1's FP32 expression, so zero-weight columns are skipped exactly;
+//     each its family, plane m and in-plane weight wb; zero-weight columns are
+//     skipped exactly;
 //   * for each voxel of the thread's z-segment, the detector rows iv inside
 //     the vertical footprint, whose width follows from the column's dq_z/div.
 // The input rt already carries K1's row weight W (rt = W * r), so a tap is
@@ -57,19 +59,23 @@ __global__ void __launch_bounds__(K2_BX *K2_BY) k2_backproject(const BpArgs a) {
         const int iu_hi = min(g.nu - 1, (int)floorf(iuc + g.hwu));
         const float *rview = a.rt + (size_t)s * view_elems;
         for (int iu = iu_lo; iu <= iu_hi; ++iu) {
-            const float4 cA = g.colA[(size_t)v * g.nu + iu];
-            const bool famY = g.colB[(size_t)v * g.nu + iu].z != 0.f;
+            const size_t col = (size_t)v * g.nu + iu;
+            const FxCol cF = g.colF[col];
+            const bool famY = g.colB[col].z != 0.f;
             const int m = famY ? j : i;
             const int bb = famY ? i : j;
-            const float fm = (float)m;
-            const float qb = fmaf(fm, cA.y, cA.x);
-            const float bf = floorf(qb);
-            const float fb = qb - bf;
-            const int b0 = (int)bf;
+            // in-plane weight, from exactly K1's crossing q_b(m)
+            const long long qb = cF.qb0 + (long long)m * cF.qb1;
+            const int b0 = fx_floor(qb);
+            const float fb = fx_frac(qb);
             const float wb = (b0 == bb) ? 1.f - fb : ((b0 + 1 == bb) ? fb : 0.f);
             if (wb == 0.f) continue;
-            const float Zc = fmaf(fm, cA.w, cA.z);  // > 0: the plane lies between source and detector
-            const float inv = 1.f / (Zc * g.dv);     // detector rows per voxel along z
+            // q_z = n*Z + cz for row iv with n = 2*iv - (nv-1); Z > 0 because the
+            // plane lies between source and detector
+            const long long Z = cF.h0 + (long long)m * cF.h1;
+            const float4 cA = g.colA[col];
+            const float Zc = fmaf((float)m, cA.w, cA.z);
+            const float inv = 1.f / (Zc * g.dv);  // detector rows per voxel along z
             const float hv = inv * 1.0001f + 1e-3f;
             const float *rcol = rview + iu;
 #pragma unroll
@@ -78,15 +84,14 @@ __global__ void __launch_bounds__(K2_BX *K2_BY) k2_backproject(const BpArgs a) {
                 const float ivs = fmaf((float)k - g.cz, inv, g.cv);
                 const int lo = max(0, (int)ceilf(ivs - hv));
                 const int hi = min(g.nv - 1, (int)floorf(ivs + hv));
+                long long qz = (long long)(2 * lo - (g.nv - 1)) * Z + g.cz_fx;
                 float sz = 0.f;
                 for (int iv = lo; iv <= hi; ++iv) {
-                    const float w = ((float)iv - g.cv) * g.dv;
-                    const float qz = fmaf(w, Zc, g.cz);
-                    const float kf = floorf(qz);
-                    const float fz = qz - kf;
-                    const int kz = (int)kf;
+                    const int kz = fx_floor(qz);
+                    const float fz = fx_frac(qz);
                     const float wz = (kz == k) ? 1.f - fz : ((kz + 1 == k) ? fz : 0.f);
                     sz = fmaf(wz, __ldg(rcol + (size_t)iv * g.nu), sz);
+                    qz += 2 * Z;
                 }
                 acc[q] = fmaf(wb, sz, acc[q]);
             }

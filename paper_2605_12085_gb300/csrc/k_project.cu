@@ -9,12 +9,13 @@
 // for one band of rows and share a z-slab of the volume in L2.
 //
 // Per-ray constants come from the geometry's column tables (FP64 on the host,
-// rounded once to FP32): q_b(m) = qb0 + m*qb1 and q_z(m) = w*(zc0 + m*zc1) + cz.
-// Every crossing is evaluated from these constants by FMA (no accumulated
-// steps).  The plane interval [m0, m1] is the exact set of planes on which the
-// FP32 crossing lies inside (-1, Nb) x (-1, nz) -- the set is an interval
-// because the rounded affine maps are monotone in m -- and the padded volume
-// layout supplies the zero border, so the inner loop has no branch.
+// rounded once to Q.40 fixed point): q_b(m) = qb0 + m*qb1 and
+// q_z(m) = n*(h0 + m*h1) + cz.  Stepping from plane to plane adds an integer,
+// so every crossing equals its closed form exactly and the gather
+// backprojector reproduces it bit for bit.  The plane interval [m0, m1] is the
+// exact set of planes on which the crossing lies inside (-1, Nb) x (-1, nz)
+// (an interval, the maps being affine in m), and the padded volume layout
+// supplies the zero border, so the inner loop has no branch.
 #include "fbl_internal.cuh"
 #include "fbl_reduce.cuh"
 
@@ -53,13 +54,17 @@ __device__ __forceinline__ void clip_affine(float c0, float c1, float lo, float 
     }
 }
 
+// One ray: FP32 constants for the plane-range estimate, exact Q.40 constants
+// for the crossings q_b(m) = qb0 + m*qb1 and q_z(m) = qz0 + m*qz1.
 struct RayConst {
-    float qb0, qb1, zc0, zc1, w, cz, Nb, Nz;
+    float fqb0, fqb1, fzc0, fzc1, w, cz, Nb, Nz;
+    long long qb0, qb1, qz0, qz1;
+    long long hi_b, hi_z;  // Nb and nz in Q.40 (the lower bound is -1)
     __device__ __forceinline__ bool inside(int m) const {
-        const float fm = (float)m;
-        const float qb = fmaf(fm, qb1, qb0);
-        const float qz = fmaf(w, fmaf(fm, zc1, zc0), cz);
-        return qb > -1.f && qb < Nb && qz > -1.f && qz < Nz;
+        const long long qb = qb0 + (long long)m * qb1;
+        const long long qz = qz0 + (long long)m * qz1;
+        constexpr long long lo = -(1LL << FX_BITS);
+        return qb > lo && qb < hi_b && qz > lo && qz < hi_z;
     }
 };
 
@@ -68,45 +73,44 @@ template <typename TX>
 __device__ __forceinline__ float ray_sum(const RayConst &rc, const TX *__restrict__ vol,
                                          const PadLayout &L) {
     float mlo = 0.f, mhi = (float)(L.Na - 1);
-    clip_affine(rc.qb0, rc.qb1, -1.f, rc.Nb, mlo, mhi);
-    clip_affine(fmaf(rc.w, rc.zc0, rc.cz), rc.w * rc.zc1, -1.f, rc.Nz, mlo, mhi);
-    if (!(mlo <= mhi)) return 0.f;
-    int m0 = max(0, (int)floorf(mlo));
-    int m1 = min(L.Na - 1, (int)ceilf(mhi));
+    clip_affine(rc.fqb0, rc.fqb1, -1.f, rc.Nb, mlo, mhi);
+    clip_affine(fmaf(rc.w, rc.fzc0, rc.cz), rc.w * rc.fzc1, -1.f, rc.Nz, mlo, mhi);
+    if (!(mlo <= mhi + 2.f)) return 0.f;
+    int m0 = max(0, (int)floorf(mlo) - 1);
+    int m1 = min(L.Na - 1, (int)ceilf(mhi) + 1);
+    // exact interval: the crossings are affine in m, so "inside" holds on an interval
     while (m0 <= m1 && !rc.inside(m0)) ++m0;
     while (m1 >= m0 && !rc.inside(m1)) --m1;
     if (m0 > m1) return 0.f;
-    if (m0 > 0 && rc.inside(m0 - 1)) --m0;
-    if (m1 < L.Na - 1 && rc.inside(m1 + 1)) ++m1;
+    while (m0 > 0 && rc.inside(m0 - 1)) --m0;
+    while (m1 < L.Na - 1 && rc.inside(m1 + 1)) ++m1;
     const int sK = L.Na * L.pitch;
-    const TX *base = vol + (sK + L.PL);  // element (b = 0, m = 0, k = 0)
+    const TX *row = vol + ((size_t)sK + L.PL + (size_t)m0 * L.pitch);  // (b = 0, m = m0, k = 0)
+    long long qb = rc.qb0 + (long long)m0 * rc.qb1;
+    long long qz = rc.qz0 + (long long)m0 * rc.qz1;
     float acc0 = 0.f, acc1 = 0.f;
     int m = m0;
     for (; m + 1 <= m1; m += 2) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int mm = m + h;
-            const float fm = (float)mm;
-            const float qb = fmaf(fm, rc.qb1, rc.qb0);
-            const float qz = fmaf(rc.w, fmaf(fm, rc.zc1, rc.zc0), rc.cz);
-            const float bf = floorf(qb), kf = floorf(qz);
-            const float fb = qb - bf, fz = qz - kf;
-            const TX *p = base + ((int)kf * sK + mm * L.pitch + (int)bf);
+            const int b0 = fx_floor(qb), k0 = fx_floor(qz);
+            const float fb = fx_frac(qb), fz = fx_frac(qz);
+            const TX *p = row + (k0 * sK + b0);
             const float v00 = ldg_f32(p), v01 = ldg_f32(p + 1);
             const float v10 = ldg_f32(p + sK), v11 = ldg_f32(p + sK + 1);
             const float lo = fmaf(fb, v01 - v00, v00);
             const float hi = fmaf(fb, v11 - v10, v10);
             const float val = fmaf(fz, hi - lo, lo);
             if (h == 0) acc0 += val; else acc1 += val;
+            qb += rc.qb1;
+            qz += rc.qz1;
+            row += L.pitch;
         }
     }
     if (m <= m1) {
-        const float fm = (float)m;
-        const float qb = fmaf(fm, rc.qb1, rc.qb0);
-        const float qz = fmaf(rc.w, fmaf(fm, rc.zc1, rc.zc0), rc.cz);
-        const float bf = floorf(qb), kf = floorf(qz);
-        const float fb = qb - bf, fz = qz - kf;
-        const TX *p = base + ((int)kf * sK + m * L.pitch + (int)bf);
+        const int b0 = fx_floor(qb), k0 = fx_floor(qz);
+        const float fb = fx_frac(qb), fz = fx_frac(qz);
+        const TX *p = row + (k0 * sK + b0);
         const float v00 = ldg_f32(p), v01 = ldg_f32(p + 1);
         const float v10 = ldg_f32(p + sK), v11 = ldg_f32(p + sK + 1);
         const float lo = fmaf(fb, v01 - v00, v00);
@@ -125,20 +129,29 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
     float r2 = 0.f;
     if (iu < g.nu && iv < g.nv) {
         const int v = a.views[s];
-        const float4 cA = g.colA[(size_t)v * g.nu + iu];
-        const float4 cB = g.colB[(size_t)v * g.nu + iu];
+        const size_t col = (size_t)v * g.nu + iu;
+        const float4 cA = g.colA[col];
+        const float4 cB = g.colB[col];
+        const FxCol cF = g.colF[col];
         const bool famY = cB.z != 0.f;
         const PadLayout &L = famY ? a.LY : a.LX;
         const TX *vol = (const TX *)(famY ? a.padY : a.padX);
+        const int n = 2 * iv - (g.nv - 1);  // w = n * dv / 2
         RayConst rc;
-        rc.qb0 = cA.x;
-        rc.qb1 = cA.y;
-        rc.zc0 = cA.z;
-        rc.zc1 = cA.w;
-        rc.w = ((float)iv - g.cv) * g.dv;
+        rc.fqb0 = cA.x;
+        rc.fqb1 = cA.y;
+        rc.fzc0 = cA.z;
+        rc.fzc1 = cA.w;
+        rc.w = (float)n * (0.5f * g.dv);
         rc.cz = g.cz;
         rc.Nb = (float)L.Nb;
         rc.Nz = (float)g.nz;
+        rc.qb0 = cF.qb0;
+        rc.qb1 = cF.qb1;
+        rc.qz0 = (long long)n * cF.h0 + g.cz_fx;
+        rc.qz1 = (long long)n * cF.h1;
+        rc.hi_b = (long long)L.Nb << FX_BITS;
+        rc.hi_z = (long long)g.nz << FX_BITS;
         const float sum = ray_sum<TX>(rc, vol, L);
         const float W = cB.x * sqrtf(fmaf(rc.w, rc.w, cB.y));
         const float ax = W * sum;
@@ -174,7 +187,7 @@ __global__ void k_weight(const DevGeom g, const TY *__restrict__ y, const int32_
     if (iu >= g.nu) return;
     const int v = views[s];
     const float4 cB = g.colB[(size_t)v * g.nu + iu];
-    const float w = ((float)iv - g.cv) * g.dv;
+    const float w = (float)(2 * iv - (g.nv - 1)) * (0.5f * g.dv);
     const float W = cB.x * sqrtf(fmaf(w, w, cB.y));
     const size_t o = ((size_t)s * g.nv + iv) * g.nu + iu;
     rt[o] = W * to_f32(y[o]);

@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def fbl():
-    from paper_2605_12085_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2605_12085_gb300 as m
     return m
 
