@@ -178,6 +178,29 @@ FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, i
                        double mu, void *xbar, double *out3_host, void *stream);
 
 /*
+ * prox_reduce_static -- the same computation and outputs as prox_reduce, for
+ * callers that must not allocate device memory: code that runs under a
+ * fixed memory budget reserved up front, host applications or plugins whose
+ * device memory is owned by someone else, and latency-critical loops where
+ * an allocation call could block or synchronize the device.  (The paper has
+ * no counterpart; this is a library-level variant.)
+ * It allocates nothing: the per-block partial sums and the three results
+ * live in one fixed device array of 1.5 MiB inside the library, which every
+ * GPU that loads the library keeps until the process exits.
+ *   - x, g and x_bar must be device memory (no host staging is possible
+ *     without allocating); other arguments as for prox_reduce.
+ *   - n <= 134217728 (2^27, a 512^3 volume); larger n returns FBL_E_INVAL.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array, and it keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race with each other and must be serialised by the caller.
+ */
+FBL_API fbl_status prox_reduce_static(const void *x, int32_t x_dtype, const float *g, int64_t n,
+                                      double alpha, double mu, void *xbar, double *out3_host,
+                                      void *stream);
+
+/*
  * fblisa_create -- a solver for Algorithm 1 on geometry g with the given
  * hyperparameters; owns its scratch (gradient, trial point, residual,
  * reduction slots) and its schedule/mini-batch state (Step 1, Step 2a).

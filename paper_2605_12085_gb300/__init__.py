@@ -69,7 +69,7 @@ PROFILE_CLASSES = ("residual_projection", "objective_projection", "gradient_back
 EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_destroy", "project", "backproject",
            "residual_norm", "prox_reduce", "fblisa_create", "fblisa_destroy", "fblisa_step",
            "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
-           "fbl_epoch_batches"]
+           "fbl_epoch_batches", "prox_reduce_static"]
 
 
 def _load():
@@ -87,6 +87,7 @@ def _load():
         "backproject": (st, [vp, vp, i32, P(i32), i32, vp, i32, vp]),
         "residual_norm": (st, [vp, vp, i32, P(i32), i32, vp, i32, P(dbl), vp]),
         "prox_reduce": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
+        "prox_reduce_static": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
         "fblisa_create": (st, [vp, P(fbl_params), P(vp)]),
         "fblisa_destroy": (None, [vp]),
         "fblisa_step": (st, [vp, vp, vp, P(fbl_step_stats), vp]),
@@ -256,6 +257,16 @@ def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):
     out = (ctypes.c_double * 3)()
     _check(lib.prox_reduce(_ptr(x), _dtype_code(x), _ptr(g), n, float(alpha), float(mu),
                            _ptr(xbar), out, _stream(x, g, xbar, stream=stream)))
+    return xbar, (out[0], out[1], out[2])
+
+
+def prox_reduce_static(x, g, alpha: float, mu: float, xbar, stream=None):
+    """prox_reduce without any allocation: x, g and xbar must be CUDA tensors
+    (xbar caller-provided); n <= 2^27.  Calls that overlap on the GPU race."""
+    n = int(np.prod(tuple(x.shape)))
+    out = (ctypes.c_double * 3)()
+    _check(lib.prox_reduce_static(_ptr(x), _dtype_code(x), _ptr(g), n, float(alpha), float(mu),
+                                  _ptr(xbar), out, _stream(x, g, xbar, stream=stream)))
     return xbar, (out[0], out[1], out[2])
 
 

@@ -1028,3 +1028,5 @@ extern "C" fbl_status fblisa_last_batch(const fbl_solver *s, int32_t *views, int
 }
 
 extern "C" const char *fbl_last_error(void) { return g_last_error.c_str(); }
+
+void fbl::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }

@@ -154,6 +154,15 @@ cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float al
                              cudaStream_t st);
 int prox_flat_num_partials(int64_t n);
 
+// The flat prox kernel on an explicit grid of nb blocks (256 threads each):
+// partials[3][nb] receives the per-block sums.
+cudaError_t launch_prox_flat_grid(const void *x, const float *gr, int64_t n, float alpha, float amu,
+                                  void *xbar, int dtype, int nb, double *partials,
+                                  cudaStream_t st);
+
+// Record the message returned by fbl_last_error() on this thread.
+void set_last_error(const char *msg);
+
 // out[c] = sum of partials[c*stride + 0 .. n) in a fixed order, for c < ncomp.
 cudaError_t launch_reduce(const double *partials, int n, int stride, int ncomp, double *out,
                           cudaStream_t st);

@@ -225,6 +225,26 @@ cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float al
     return cudaGetLastError();
 }
 
+cudaError_t launch_prox_flat_grid(const void *x, const float *gr, int64_t n, float alpha, float amu,
+                                  void *xbar, int dtype, int nb, double *partials,
+                                  cudaStream_t st) {
+    switch (dtype) {
+        case FBL_BF16:
+            k_prox_flat<<<nb, F_NT, 0, st>>>((const __nv_bfloat16 *)x, gr, n, alpha, amu,
+                                             (__nv_bfloat16 *)xbar, partials);
+            break;
+        case FBL_F16:
+            k_prox_flat<<<nb, F_NT, 0, st>>>((const __half *)x, gr, n, alpha, amu, (__half *)xbar,
+                                             partials);
+            break;
+        default:
+            k_prox_flat<<<nb, F_NT, 0, st>>>((const float *)x, gr, n, alpha, amu, (float *)xbar,
+                                             partials);
+            break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double *partials, int n, int stride, int ncomp, double *out,
                           cudaStream_t st) {
     k_reduce<<<ncomp, R_NT, 0, st>>>(partials, n, stride, out);
