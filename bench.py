@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 METRIC = "GUPS fwd+back at 512^3/720 views; FB-LISA time-to-1e-3 rel-err vs plain FP32"
 UNIT = "GUPS"
 OPS_PER_SAMPLE = 14      # FP32 ops of one Joseph sample (K1)
-K3_BYTES_PER_VOXEL = 16  # read x, g; write x_bar in two layouts (FP32)
+K3_BYTES_PER_VOXEL = 12  # read x and g, write x_bar (FP32)
 
 
 def parse():
@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "backtracks_per_step": statistics.mean(st["backtracks"] for st in stats),
            "roofline": roofline,
-           "roofline_k3": {"kernel": "k_prox_padded", "bound": "hbm", "achieved": k3_gbs,
+           "roofline_k3": {"kernel": "k_prox_zi", "bound": "hbm", "achieved": k3_gbs,
                            "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                            "frac": (k3_gbs / peaks["hbm_gbs"]) if k3_gbs else None,
                            "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},

@@ -102,10 +102,9 @@ struct fbl_geometry {
 
 namespace {
 
-PadLayout layout_for(const fbl_geometry *g, int fam, int dtype) {
+ZLayout layout_for(const fbl_geometry *g, int dtype) {
     const fbl_geometry_desc &d = g->desc;
-    return fam ? make_layout(d.ny, d.nx, d.nz, dtype_size(dtype))
-               : make_layout(d.nx, d.ny, d.nz, dtype_size(dtype));
+    return make_layout(d.nx, d.ny, d.nz, dtype_size(dtype));
 }
 
 double view_angle(const fbl_geometry_desc &d, const std::vector<double> &ang, int v) {
@@ -146,12 +145,11 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     if (!(rxy + slack < d.sod && rxy + slack < d.sdd - d.sod))
         return fail(FBL_E_UNSUPPORTED,
                     "geometry_create: the volume must lie strictly between source and detector");
-    for (int fam = 0; fam < 2; ++fam)
-        for (int es : {2, 4}) {
-            PadLayout L = fam ? make_layout(d.ny, d.nx, d.nz, es) : make_layout(d.nx, d.ny, d.nz, es);
-            if (L.elems() >= (int64_t(1) << 31))
-                return fail(FBL_E_UNSUPPORTED, "geometry_create: volume too large for 32-bit indexing");
-        }
+    for (int es : {2, 4}) {
+        const ZLayout L = make_layout(d.nx, d.ny, d.nz, es);
+        if (L.elems() >= (int64_t(1) << 31))
+            return fail(FBL_E_UNSUPPORTED, "geometry_create: volume too large for 32-bit indexing");
+    }
     auto g = new fbl_geometry();
     g->desc = d;
     if (d.angles) {
@@ -179,13 +177,13 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     std::vector<FxCol> colF(ncol);
     auto fx = [](double v) { return (long long)std::llround(v * FX_ONE); };
     std::vector<float2> trig(d.n_views);
-    double hw = 0.0;
+    double hw = 0.0, max_inv = 0.0;
     for (int v = 0; v < d.n_views; ++v) {
         const double th = view_angle(d, g->angles, v);
         const double c = std::cos(th), sn = std::sin(th);
         trig[v] = make_float2((float)c, (float)sn);
         const double s[2] = {d.sod * c, d.sod * sn};
-        std::vector<double> qb_first(d.nu), qb_last(d.nu);
+        std::vector<double> m_in_lo(d.nu), m_in_hi(d.nu), qb0v(d.nu), qb1v(d.nu);
         std::vector<int> famv(d.nu);
         for (int iu = 0; iu < d.nu; ++iu) {
             // d = P - s with P = c_det + u e_u, written in the definition's order so
@@ -212,16 +210,42 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
             colA[(size_t)v * d.nu + iu] = make_float4((float)qb0, (float)qb1, (float)zc0, (float)zc1);
             colF[(size_t)v * d.nu + iu] = FxCol{fx(qb0), fx(qb1), fx(0.5 * d.dv * zc0), fx(0.5 * d.dv * zc1)};
             colB[(size_t)v * d.nu + iu] = make_float4((float)wa, (float)h2, (float)fam, 0.f);
-            qb_first[iu] = qb0;
-            qb_last[iu] = qb0 + (Nn[a] - 1) * qb1;
             famv[iu] = fam;
+            // planes on which this column's crossing is inside the volume: -1 < q_b < Nb
+            double mlo = 0, mhi = Nn[a] - 1;
+            if (qb1 > 0) {
+                mlo = std::max(mlo, (-1.0 - qb0) / qb1);
+                mhi = std::min(mhi, ((double)Nn[b] - qb0) / qb1);
+            } else if (qb1 < 0) {
+                mlo = std::max(mlo, ((double)Nn[b] - qb0) / qb1);
+                mhi = std::min(mhi, (-1.0 - qb0) / qb1);
+            } else if (!(qb0 > -1.0 && qb0 < Nn[b])) {
+                mlo = 1;
+                mhi = 0;
+            }
+            m_in_lo[iu] = mlo;
+            m_in_hi[iu] = mhi;
+            qb0v[iu] = qb0;
+            qb1v[iu] = qb1;
+            // detector rows per voxel along z where the column meets the volume:
+            // 1/(dv*Zc(m)), Zc affine in m
+            if (mlo <= mhi)
+                for (double m : {mlo, mhi}) {
+                    const double Zc = zc0 + m * zc1;
+                    if (Zc > 0) max_inv = std::max(max_inv, 1.0 / (d.dv * Zc));
+                }
         }
+        // columns per voxel in-plane (the candidate window K2 searches): the
+        // inverse step of q_b between neighbouring columns, where both meet the volume
         for (int iu = 0; iu + 1 < d.nu; ++iu) {
             if (famv[iu] != famv[iu + 1]) continue;
-            const double d0 = std::fabs(qb_first[iu + 1] - qb_first[iu]);
-            const double d1 = std::fabs(qb_last[iu + 1] - qb_last[iu]);
-            const double dm = std::min(d0, d1);
-            if (dm > 0) hw = std::max(hw, 1.0 / dm);
+            const double lo = std::max(m_in_lo[iu], m_in_lo[iu + 1]);
+            const double hi = std::min(m_in_hi[iu], m_in_hi[iu + 1]);
+            if (lo > hi) continue;
+            for (double m : {lo, hi}) {
+                const double dq = std::fabs((qb0v[iu + 1] + m * qb1v[iu + 1]) - (qb0v[iu] + m * qb1v[iu]));
+                if (dq > 0) hw = std::max(hw, 1.0 / dq);
+            }
         }
     }
     if (hw == 0.0) hw = (double)d.nu;  // a single column: take every column as a candidate
@@ -249,6 +273,14 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     dg.inv_du = (float)(1.0 / d.du);
     dg.hwu = (float)hw;
     dg.cz_fx = (long long)std::llround(cxyz[2] * FX_ONE);
+    // detector rows with a crossing in (k - 1, k + 1) on one column: at most
+    // floor(2 max_inv) + 1
+    dg.ntap = (int)std::floor(2.0 * max_inv * 1.0001 + 0.002) + 1;
+    if (dg.ntap > RT_PAD) {
+        geometry_destroy(g);
+        return fail(FBL_E_UNSUPPORTED, "geometry_create: detector rows finer than %d per voxel",
+                    RT_PAD);
+    }
 
     e = cudaMalloc(&g->d_colA, ncol * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colB, ncol * sizeof(float4));
@@ -401,17 +433,14 @@ fbl_status device_input(const void *p, size_t bytes, AsyncBuf &stage, const void
     return FBL_OK;
 }
 
-// Padded copies of a caller volume (both layouts), stream-ordered.
-fbl_status pack_volume(const fbl_geometry *g, const void *xdev, int dtype, AsyncBuf &pY,
-                       AsyncBuf &pX, PadLayout &LY, PadLayout &LX, cudaStream_t st) {
-    LY = layout_for(g, 1, dtype);
-    LX = layout_for(g, 0, dtype);
-    const int es = dtype_size(dtype);
-    CK(pY.alloc((size_t)LY.elems() * es, st), "padded volume");
-    CK(pX.alloc((size_t)LX.elems() * es, st), "padded volume");
-    CK(cudaMemsetAsync(pY.p, 0, (size_t)LY.elems() * es, st), "memset");
-    CK(cudaMemsetAsync(pX.p, 0, (size_t)LX.elems() * es, st), "memset");
-    CK(launch_pack(xdev, dtype, g->desc.nx, g->desc.ny, g->desc.nz, pY.p, LY, pX.p, LX, st), "pack");
+// The library layout of a caller volume, stream-ordered.
+fbl_status pack_volume(const fbl_geometry *g, const void *xdev, int dtype, AsyncBuf &pv,
+                       ZLayout &L, cudaStream_t st) {
+    L = layout_for(g, dtype);
+    const size_t bytes = (size_t)L.elems() * dtype_size(dtype);
+    CK(pv.alloc(bytes, st), "volume layout");
+    CK(cudaMemsetAsync(pv.p, 0, bytes, st), "memset");
+    CK(launch_pack(xdev, dtype, pv.p, L, st), "pack");
     return FBL_OK;
 }
 
@@ -430,19 +459,19 @@ extern "C" fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dt
     const fbl_geometry_desc &d = g->desc;
     const size_t nvox = (size_t)d.nx * d.ny * d.nz;
     const size_t ny_out = (size_t)n_sel * d.nv * d.nu;
-    AsyncBuf dviews, xs, pY, pX, ys;
+    AsyncBuf dviews, xs, pv, ys;
     if ((st = upload_views(views, n_sel, dviews, s))) return st;
     const void *xd = nullptr;
     if ((st = device_input(x, nvox * dtype_size(x_dtype), xs, &xd, s))) return st;
-    PadLayout LY, LX;
-    if ((st = pack_volume(g, xd, x_dtype, pY, pX, LY, LX, s))) return st;
+    ZLayout L;
+    if ((st = pack_volume(g, xd, x_dtype, pv, L, s))) return st;
     const bool y_dev = is_device_ptr(y);
     void *yd = y;
     if (!y_dev) {
         CK(ys.alloc(ny_out * dtype_size(y_dtype), s), "output staging");
         yd = ys.p;
     }
-    CK(launch_project(PROJ_STORE, g->dg, pX.p, LX, pY.p, LY, x_dtype, (const int32_t *)dviews.p,
+    CK(launch_project(PROJ_STORE, g->dg, pv.p, L, x_dtype, (const int32_t *)dviews.p,
                       n_sel, nullptr, FBL_F32, nullptr, yd, y_dtype, nullptr, nullptr, s),
        "project kernel");
     if (!y_dev) {
@@ -465,7 +494,7 @@ extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t 
     const size_t nvox = (size_t)d.nx * d.ny * d.nz;
     const size_t ny_in = (size_t)n_sel * d.nv * d.nu;
     const bool x_dev = is_device_ptr(x);
-    AsyncBuf dviews, ys, rt, xs;
+    AsyncBuf dviews, ys, rt, xs, gz;
     float *xd = x;
     if (!x_dev) {
         CK(xs.alloc(nvox * sizeof(float), s), "output staging");
@@ -478,12 +507,16 @@ extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t 
         if ((st = upload_views(views, n_sel, dviews, s))) return st;
         const void *yd = nullptr;
         if ((st = device_input(y, ny_in * dtype_size(y_dtype), ys, &yd, s))) return st;
-        CK(rt.alloc(ny_in * sizeof(float), s), "weighted sinogram");
+        const size_t rt_elems = (size_t)n_sel * d.nu * rt_pitch(d.nv);
+        CK(rt.alloc(rt_elems * sizeof(float), s), "weighted sinogram");
+        CK(cudaMemsetAsync(rt.p, 0, rt_elems * sizeof(float), s), "memset");
         CK(launch_weight(g->dg, yd, y_dtype, (const int32_t *)dviews.p, n_sel, (float *)rt.p, s),
            "weight kernel");
-        CK(launch_backproject(g->dg, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f, xd,
-                              accumulate, s),
+        CK(gz.alloc(nvox * sizeof(float), s), "gradient scratch");
+        CK(launch_backproject(g->dg, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f,
+                              (float *)gz.p, s),
            "backproject kernel");
+        CK(launch_zi_to_natural((const float *)gz.p, xd, d.nx, d.ny, d.nz, accumulate, s), "reorder");
     }
     if (!x_dev) {
         CK(cudaMemcpyAsync(x, xd, nvox * sizeof(float), cudaMemcpyDeviceToHost, s), "x D2H");
@@ -534,12 +567,12 @@ extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_
     cudaStream_t s = (cudaStream_t)stream;
     const fbl_geometry_desc &d = g->desc;
     const size_t nvox = (size_t)d.nx * d.ny * d.nz;
-    AsyncBuf dviews, xs, pY, pX, bs, part, res;
+    AsyncBuf dviews, xs, pv, bs, part, res;
     if ((st = upload_views(views, n_sel, dviews, s))) return st;
     const void *xd = nullptr;
     if ((st = device_input(x, nvox * dtype_size(x_dtype), xs, &xd, s))) return st;
-    PadLayout LY, LX;
-    if ((st = pack_volume(g, xd, x_dtype, pY, pX, LY, LX, s))) return st;
+    ZLayout L;
+    if ((st = pack_volume(g, xd, x_dtype, pv, L, s))) return st;
     const void *bd = nullptr;
     const int32_t *bmap = nullptr;
     if ((st = batch_data(g, b, b_dtype, views, (const int32_t *)dviews.p, n_sel, bs, &bd, &bmap, s)))
@@ -547,7 +580,7 @@ extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_
     const int np = project_num_partials(g->dg, n_sel);
     CK(part.alloc((size_t)np * sizeof(double), s), "partials");
     CK(res.alloc(sizeof(double), s), "result");
-    CK(launch_project(PROJ_NORM, g->dg, pX.p, LX, pY.p, LY, x_dtype, (const int32_t *)dviews.p, n_sel,
+    CK(launch_project(PROJ_NORM, g->dg, pv.p, L, x_dtype, (const int32_t *)dviews.p, n_sel,
                       bd, b_dtype, bmap, nullptr, FBL_F32, (double *)part.p, nullptr, s),
        "objective kernel");
     CK(launch_reduce((const double *)part.p, np, np, 1, (double *)res.p, s), "reduce");
@@ -609,11 +642,11 @@ struct fbl_solver {
     std::vector<int32_t> epoch_views;
     std::vector<int32_t> last_batch;
     // device state
-    PadLayout LY, LX;
-    size_t padY_bytes = 0, padX_bytes = 0;
-    void *stY = nullptr, *stX = nullptr, *trY = nullptr, *trX = nullptr;
-    float *grad = nullptr;
-    float *rt = nullptr;
+    ZLayout L;                     // z-innermost layout of the iterates
+    size_t vol_bytes = 0;
+    void *st = nullptr, *tr = nullptr;  // current iterate x and trial point x_bar
+    float *grad = nullptr;              // gradient, [j][i][k]
+    float *rt = nullptr;                // weighted residual rt[s][iu][RT_PAD + iv]
     size_t rt_cap = 0;
     void *bstage = nullptr;
     size_t bstage_cap = 0;
@@ -636,10 +669,8 @@ struct fbl_solver {
 namespace {
 
 void solver_free(fbl_solver *s) {
-    cudaFree(s->stY);
-    cudaFree(s->stX);
-    cudaFree(s->trY);
-    cudaFree(s->trX);
+    cudaFree(s->st);
+    cudaFree(s->tr);
     cudaFree(s->grad);
     cudaFree(s->rt);
     cudaFree(s->bstage);
@@ -689,16 +720,17 @@ void prof_flush(fbl_solver *s) {
 
 fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
     const fbl_geometry_desc &d = s->g->desc;
-    const size_t need = (size_t)N * d.nv * d.nu;
+    const size_t need = (size_t)N * d.nu * rt_pitch(d.nv);
     if (need > s->rt_cap) {
         cudaFree(s->rt);
         s->rt = nullptr;
         s->rt_cap = 0;
         CK(cudaMalloc(&s->rt, need * sizeof(float)), "residual buffer");
+        CK(cudaMemset(s->rt, 0, need * sizeof(float)), "residual buffer");  // zero row pads
         s->rt_cap = need;
     }
     const size_t np = std::max((size_t)project_num_partials(s->g->dg, N),
-                               (size_t)3 * prox_padded_num_partials(d.nx, d.ny, d.nz));
+                               (size_t)3 * prox_zi_num_partials(d.nx, d.ny, d.nz));
     if (np > s->partials_cap) {
         cudaFree(s->partials);
         s->partials = nullptr;
@@ -723,7 +755,7 @@ void begin_epoch_if_needed(fbl_solver *s) {
     batches(s->p.seed, s->epoch, d.n_views, s->N_t, s->epoch_views);
 }
 
-// One iteration of Algorithm 1 on the solver's padded state (stY/stX).
+// One iteration of Algorithm 1 on the solver's state (s->st).
 fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_stats *stats,
                           cudaStream_t st) {
     const fbl_geometry *g = s->g;
@@ -783,14 +815,14 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     // Step 2b: residual, f_N(x), grad f_N(x)
     int np = 0;
     CK(prof_launch(s, 0, st, [&] {
-           return launch_project(PROJ_RESID, g->dg, s->stX, s->LX, s->stY, s->LY, xdt, s->d_views, N,
+           return launch_project(PROJ_RESID, g->dg, s->st, s->L, xdt, s->d_views, N,
                                  bd, s->p.b_dtype, bmap, s->rt, FBL_F32, s->partials, &np, st);
        }),
        "residual kernel");
     CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
        "reduce");
     CK(prof_launch(s, 2, st, [&] {
-           return launch_backproject(g->dg, s->rt, s->d_views, N, (float)scale, s->grad, 0, st);
+           return launch_backproject(g->dg, s->rt, s->d_views, N, (float)scale, s->grad, st);
        }),
        "gradient kernel");
     // Step 2c: backtracking on (2.3)
@@ -804,15 +836,14 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     for (bt = 0; bt <= s->p.max_backtracks; ++bt) {
         int npp = 0;
         CK(prof_launch(s, 3, st, [&] {
-               return launch_prox_padded(s->stY, s->LY, s->grad, (float)alpha, (float)(alpha * s->p.mu),
-                                         s->trY, s->trX, s->LX, xdt, d.nx, d.ny, d.nz, s->partials,
-                                         &npp, st);
+               return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu),
+                                     s->tr, xdt, s->partials, &npp, st);
            }),
            "prox kernel");
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
            "reduce");
         CK(prof_launch(s, 1, st, [&] {
-               return launch_project(PROJ_NORM, g->dg, s->trX, s->LX, s->trY, s->LY, xdt, s->d_views, N,
+               return launch_project(PROJ_NORM, g->dg, s->tr, s->L, xdt, s->d_views, N,
                                      bd, s->p.b_dtype, bmap, nullptr, FBL_F32, s->partials, &np, st);
            }),
            "objective kernel");
@@ -859,9 +890,8 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         return fail(FBL_E_LINESEARCH, "fblisa_step: no step passed (2.3) within %d backtracks",
                     s->p.max_backtracks);
     }
-    // Step 2d: x <- x_bar (swap the padded buffers); alpha restarts from alpha_0.
-    std::swap(s->stY, s->trY);
-    std::swap(s->stX, s->trX);
+    // Step 2d: x <- x_bar (swap the state and trial buffers); alpha restarts from alpha_0.
+    std::swap(s->st, s->tr);
     s->k += 1;
     s->iter_in_epoch += 1;
     return FBL_OK;
@@ -876,7 +906,7 @@ fbl_status solver_load_x(fbl_solver *s, const void *x, bool x_dev, cudaStream_t 
         src = s->xstage;
     }
     CK(prof_launch(s, 5, st, [&] {
-           return launch_pack(src, s->p.x_dtype, d.nx, d.ny, d.nz, s->stY, s->LY, s->stX, s->LX, st);
+           return launch_pack(src, s->p.x_dtype, s->st, s->L, st);
        }),
        "pack");
     return FBL_OK;
@@ -884,12 +914,17 @@ fbl_status solver_load_x(fbl_solver *s, const void *x, bool x_dev, cudaStream_t 
 
 fbl_status solver_store_x(fbl_solver *s, void *x, bool x_dev, cudaStream_t st) {
     const fbl_geometry_desc &d = s->g->desc;
-    const int es = dtype_size(s->p.x_dtype);
-    const size_t bytes = (size_t)d.nx * d.ny * d.nz * es;
+    const size_t bytes = (size_t)d.nx * d.ny * d.nz * dtype_size(s->p.x_dtype);
     if (x_dev) {
-        CK(copy_unpad(s->stY, s->LY, es, x, d.nx, d.ny, d.nz, st), "x copy");
+        CK(prof_launch(s, 5, st, [&] {
+               return launch_unpack(s->st, s->L, s->p.x_dtype, x, st);
+           }),
+           "x copy");
     } else {
-        CK(copy_unpad(s->stY, s->LY, es, s->xstage, d.nx, d.ny, d.nz, st), "x copy");
+        CK(prof_launch(s, 5, st, [&] {
+               return launch_unpack(s->st, s->L, s->p.x_dtype, s->xstage, st);
+           }),
+           "x copy");
         CK(cudaMemcpyAsync(x, s->xstage, bytes, cudaMemcpyDeviceToHost, st), "x D2H");
     }
     CK(cudaStreamSynchronize(st), "x store");
@@ -919,18 +954,15 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     s->p = *p;
     s->device = g->device;
     s->n_max = n_max;
-    s->LY = layout_for(g, 1, p->x_dtype);
-    s->LX = layout_for(g, 0, p->x_dtype);
+    s->L = layout_for(g, p->x_dtype);
     const int es = dtype_size(p->x_dtype);
-    s->padY_bytes = (size_t)s->LY.elems() * es;
-    s->padX_bytes = (size_t)s->LX.elems() * es;
+    s->vol_bytes = (size_t)s->L.elems() * es;
     const size_t nvox = (size_t)d.nx * d.ny * d.nz;
     cudaError_t e = cudaSuccess;
-    void **pads[4] = {&s->stY, &s->trY, &s->stX, &s->trX};
-    const size_t padb[4] = {s->padY_bytes, s->padY_bytes, s->padX_bytes, s->padX_bytes};
-    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
-        e = cudaMalloc(pads[q], padb[q]);
-        if (e == cudaSuccess) e = cudaMemset(*pads[q], 0, padb[q]);
+    void **vols[2] = {&s->st, &s->tr};
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaMalloc(vols[q], s->vol_bytes);
+        if (e == cudaSuccess) e = cudaMemset(*vols[q], 0, s->vol_bytes);  // zero border, once
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, nvox * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->xstage, nvox * es);

@@ -31,38 +31,49 @@ template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return
 template <typename T> __device__ __forceinline__ float ldg_f32(const T *p) { return to_f32(__ldg(p)); }
 
 // ---------------------------------------------------------------------------
-// Padded volume layouts used by the projector.
+// Volume layout used inside the library (z innermost, zero border).
 //
-// A ray of family f crosses the planes m of its dominant axis a (a = x for
-// f = 0, a = y for f = 1); in-plane it moves along the other horizontal axis
-// b and along z.  Family f reads a copy of the volume laid out as
-//     P_f[k + 1][m][b + PL]      (k in [-1, nz], m in [0, Na), b in [-PL, pitch-PL))
-// with zeros outside the volume, so the bilinear footprint of any crossing
-// with -1 < q_b < Nb and -1 < q_z < nz reads in bounds and sees zero padding
-// without a branch.  PL = 16 bytes of elements keeps the interior of every
-// row 16-byte aligned; pitch is a multiple of PL with at least one zero after
-// the last element.
+//     V[j + 1][i + 1][k + PL]   (j in [-1, ny], i in [-1, nx], k in [-PL, pitch-PL))
+//
+// Everything outside the volume (i or j at -1 or n, k < 0, k >= nz) is zero.
+// A ray of family f crosses the planes m of its dominant axis (m = i for
+// x-planes, m = j for y-planes) and moves in-plane along the other horizontal
+// axis b and along z; both families read this one copy, with the plane and
+// in-plane strides swapped.  The detector rows of one column (a warp of K1)
+// sample consecutive k.  A bilinear footprint with -1 < q_b < Nb and
+// -1 < q_z < nz reads in bounds and sees the zero boundary without a branch.
+// PL = 16 bytes of elements keeps each row's interior 16-byte aligned; pitch
+// is a multiple of PL with at least one zero after the last element.
+// The gradient uses the unpadded z-innermost order [j][i][k].
 // ---------------------------------------------------------------------------
-struct PadLayout {
-    int Na, Nb, nz;
-    int PL;      // left pad, elements
-    int pitch;   // row pitch, elements
-    __host__ __device__ int64_t elems() const { return (int64_t)(nz + 2) * Na * pitch; }
-    __host__ __device__ int64_t index(int b, int m, int k) const {
-        return ((int64_t)(k + 1) * Na + m) * pitch + b + PL;
+struct ZLayout {
+    int nx, ny, nz;
+    int PL;      // left pad along k, elements
+    int pitch;   // row length, elements
+    __host__ __device__ int64_t elems() const { return (int64_t)(ny + 2) * (nx + 2) * pitch; }
+    __host__ __device__ int64_t index(int i, int j, int k) const {
+        return ((int64_t)(j + 1) * (nx + 2) + (i + 1)) * pitch + k + PL;
     }
+    // strides of a family: y-planes (plane j, in-plane i) or x-planes (plane i, in-plane j)
+    __host__ __device__ int plane_stride(bool famY) const { return famY ? (nx + 2) * pitch : pitch; }
+    __host__ __device__ int inplane_stride(bool famY) const { return famY ? pitch : (nx + 2) * pitch; }
 };
 
-inline PadLayout make_layout(int Na, int Nb, int nz, int esize) {
-    PadLayout L;
-    L.Na = Na;
-    L.Nb = Nb;
+inline ZLayout make_layout(int nx, int ny, int nz, int esize) {
+    ZLayout L;
+    L.nx = nx;
+    L.ny = ny;
     L.nz = nz;
     L.PL = 16 / esize;
-    int need = L.PL + Nb + 1;
+    const int need = L.PL + nz + 1;
     L.pitch = (need + L.PL - 1) / L.PL * L.PL;
     return L;
 }
+
+// Transposed residual / weighted sinogram: rt[s][iu][RT_PAD + iv], rows of
+// nv + 2*RT_PAD floats whose RT_PAD leading and trailing entries are zero.
+constexpr int RT_PAD = 8;
+__host__ __device__ inline int rt_pitch(int nv) { return nv + 2 * RT_PAD; }
 
 // ---------------------------------------------------------------------------
 // Geometry tables on the device.
@@ -104,6 +115,7 @@ struct DevGeom {
     float vx, vy, vz;            // voxel size
     float sod, sdd, inv_du;
     float hwu;                   // half width, in columns, of a voxel's column footprint
+    int ntap;                    // detector rows that can touch one voxel in one column
     long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
     const FxCol *colF;           // [n_views][nu] exact fixed-point constants
@@ -114,39 +126,43 @@ struct DevGeom {
 enum ProjMode { PROJ_STORE = 0, PROJ_RESID = 1, PROJ_NORM = 2 };
 
 // Kernel launchers (each returns the launch error, if any).
-cudaError_t launch_pack(const void *x, int x_dtype, int nx, int ny, int nz, void *padY,
-                        PadLayout LY, void *padX, PadLayout LX, cudaStream_t st);
 
-// mode STORE: out[s] = A_{views[s]} x  (out_dtype)
-// mode RESID: out[s] = W * (A x - b[bview(s)]) as float32, partials += r^2
+// Natural [nz][ny][nx] volume -> the library layout (interior only).
+cudaError_t launch_pack(const void *x, int x_dtype, void *vol, ZLayout L, cudaStream_t st);
+// Library layout -> natural [nz][ny][nx] (same dtype).
+cudaError_t launch_unpack(const void *vol, ZLayout L, int dtype, void *x, cudaStream_t st);
+// Gradient order [j][i][k] (float) -> natural [nz][ny][nx] float, = or +=.
+cudaError_t launch_zi_to_natural(const float *gzi, float *x, int nx, int ny, int nz, int accumulate,
+                                 cudaStream_t st);
+
+// mode STORE: out[s][iv][iu] = A_{views[s]} x  (out_dtype)
+// mode RESID: out = rt[s][iu][RT_PAD + iv] = W * (A x - b) as float32, partials += r^2
 // mode NORM:  partials += (A x - b)^2 only
 // b_views: device list mapping slot s to the view index inside b (NULL: b is
-// already the batch, slot s at index s).
-cudaError_t launch_project(int mode, const DevGeom &g, const void *padX, PadLayout LX,
-                           const void *padY, PadLayout LY, int x_dtype, const int32_t *views,
+// already the batch, slot s at index s).  b is [view][nv][nu].
+cudaError_t launch_project(int mode, const DevGeom &g, const void *vol, ZLayout L, int x_dtype,
+                           const int32_t *views,
                            int n_sel, const void *b, int b_dtype, const int32_t *b_views,
                            void *out, int out_dtype, double *partials, int *n_partials,
                            cudaStream_t st);
 int project_num_partials(const DevGeom &g, int n_sel);
 
-// rt[s][iv][iu] = W(ray) * y[s][iv][iu] (the row weight folded in for K2)
+// rt[s][iu][RT_PAD + iv] = W(ray) * y[s][iv][iu] (the row weight folded in for K2);
+// the pad entries are left untouched (the caller zeroes them once).
 cudaError_t launch_weight(const DevGeom &g, const void *y, int y_dtype, const int32_t *views,
                           int n_sel, float *rt, cudaStream_t st);
 
-// g[k][j][i] = scale * sum over listed views of the transpose taps of rt
-// (+= when accumulate).
+// gzi[j][i][k] = scale * sum over listed views of the transpose taps of rt.
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
-                               int n_sel, float scale, float *gout, int accumulate,
-                               cudaStream_t st);
+                               int n_sel, float scale, float *gzi, cudaStream_t st);
 
-// x_bar = max(x - alpha*gr - alpha*mu, 0) for the solver's padded state:
-// reads padY (current x), gr (natural layout), writes trialY / trialX;
-// partials[3][nblk] = (g^T d, d^T d, |x_bar|_1) per block.
-cudaError_t launch_prox_padded(const void *padY, PadLayout LY, const float *gr, float alpha,
-                               float amu, void *trialY, void *trialX, PadLayout LX, int dtype,
-                               int nx, int ny, int nz, double *partials, int *n_partials,
-                               cudaStream_t st);
-int prox_padded_num_partials(int nx, int ny, int nz);
+// x_bar = max(x - alpha*g - alpha*mu, 0) on the solver's state: reads vol
+// (current x) and gzi, writes trial; partials[3][nblk] =
+// (g^T d, d^T d, |x_bar|_1) per block.
+cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu,
+                           void *trial, int dtype, double *partials, int *n_partials,
+                           cudaStream_t st);
+int prox_zi_num_partials(int nx, int ny, int nz);
 
 // Flat prox on n elements (public prox_reduce).
 cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float alpha, float amu,
@@ -166,9 +182,5 @@ void set_last_error(const char *msg);
 // out[c] = sum of partials[c*stride + 0 .. n) in a fixed order, for c < ncomp.
 cudaError_t launch_reduce(const double *partials, int n, int stride, int ncomp, double *out,
                           cudaStream_t st);
-
-// Copy the interior of a padded Y-layout volume to a natural [nz][ny][nx] one.
-cudaError_t copy_unpad(const void *padY, PadLayout LY, int esize, void *x, int nx, int ny, int nz,
-                       cudaStream_t st);
 
 }  // namespace fbl

@@ -1,31 +1,34 @@
 // K2 -- exact transpose A_N^T of the mini-batch projector (Step 2b's
 // grad f_N = (n_theta/N_t) A_N^T (A_N x - b_N), eq. (2.5)) on sm_103a, in
-// gather form: every voxel collects the taps that K1 would have given it.
+// gather form: every voxel collects the taps that K1 gives it.  No atomics.
 //
 // A ray of family f touches voxel (i, j, k) only on the plane m of its
 // dominant axis that contains the voxel (m = i for x-planes, m = j for
 // y-planes), with weight wb * wz: wb from the in-plane crossing q_b(m) of its
-// column and wz from the vertical crossing q_z(m).  Both crossings are the
-// exact Q.40 fixed-point numbers K1 steps through, so the two kernels use the
-// same weights bit for bit.  The gather enumerates
-//   * the detector columns iu within hwu of the voxel centre's projection
-//     (a geometry-wide bound on the footprint, computed on the host), and for
-//     each its family, plane m and in-plane weight wb; zero-weight columns are
-//     skipped exactly;
-//   * for each voxel of the thread's z-segment, the detector rows iv inside
-//     the vertical footprint, whose width follows from the column's dq_z/div.
-// The input rt already carries K1's row weight W (rt = W * r), so a tap is
-// one FMA.  A thread owns a z-segment of one voxel column (i, j) and keeps the
-// segment's sums in registers; lanes of a warp are consecutive i, so the
-// gradient is written coalesced.  No atomics are used.
+// detector column, wz from the vertical crossing q_z(m) of its row.
+//
+// Work decomposition.  A warp owns 128 voxels of one (i, j) column along z
+// (lane l holds k = k0 + l + 32q, q < 4).  Everything that depends only on
+// (i, j) and the view -- the candidate columns within hwu of the voxel
+// column's projection, each column's family, plane m, exact in-plane weight
+// wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
+// over the warp.  Per voxel, the detector rows that can reach it lie among the
+// ntap rows starting at the first row of its vertical footprint; the offset
+// q_z - k of the first is taken exactly from the Q.40 crossing and the next
+// ones follow by the exact per-row step, so wz = max(0, 1 - |q_z - k|) is
+// accurate to a few 1e-7.  The residual arrives transposed and zero-padded
+// (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
+// lanes' row reads are contiguous and need no bounds test.  The gradient is
+// written in z-innermost order [j][i][k], coalesced.
 #include "fbl_internal.cuh"
 
 namespace fbl {
 namespace {
 
-constexpr int K2_BX = 32;
-constexpr int K2_BY = 4;
-constexpr int K2_KS = 8;  // voxels per thread along z
+constexpr int K2_LANES = 32;
+constexpr int K2_WARPS = 8;   // consecutive i per block
+constexpr int K2_VPL = 4;     // voxels per lane
+constexpr int K2_KSPAN = K2_LANES * K2_VPL;
 
 struct BpArgs {
     DevGeom g;
@@ -33,22 +36,24 @@ struct BpArgs {
     const int32_t *views;
     int n_sel;
     float scale;
-    float *gout;
-    int accumulate;
+    float *gzi;
 };
 
-__global__ void __launch_bounds__(K2_BX *K2_BY) k2_backproject(const BpArgs a) {
+__global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
     const DevGeom &g = a.g;
-    const int i = blockIdx.x * K2_BX + threadIdx.x;
-    const int j = blockIdx.y * K2_BY + threadIdx.y;
-    const int k0 = blockIdx.z * K2_KS;
-    if (i >= g.nx || j >= g.ny) return;
-    float acc[K2_KS];
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
+    const int j = blockIdx.y;
+    const int kbase = blockIdx.z * K2_KSPAN + lane;
+    if (i >= g.nx) return;
+    float acc[K2_VPL];
 #pragma unroll
-    for (int q = 0; q < K2_KS; ++q) acc[q] = 0.f;
+    for (int q = 0; q < K2_VPL; ++q) acc[q] = 0.f;
     const float xc = ((float)i - g.cx) * g.vx;
     const float yc = ((float)j - g.cy) * g.vy;
-    const size_t view_elems = (size_t)g.nv * g.nu;
+    const int rp = rt_pitch(g.nv);
+    const int lo_max = g.nv + RT_PAD - g.ntap;  // last first-row whose taps stay in the pad
+    constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
     for (int s = 0; s < a.n_sel; ++s) {
         const int v = a.views[s];
         const float2 cs = g.trig[v];
@@ -57,72 +62,75 @@ __global__ void __launch_bounds__(K2_BX *K2_BY) k2_backproject(const BpArgs a) {
         const float iuc = eta * (g.sdd / (g.sod - xi)) * g.inv_du + g.cu;
         const int iu_lo = max(0, (int)ceilf(iuc - g.hwu));
         const int iu_hi = min(g.nu - 1, (int)floorf(iuc + g.hwu));
-        const float *rview = a.rt + (size_t)s * view_elems;
         for (int iu = iu_lo; iu <= iu_hi; ++iu) {
             const size_t col = (size_t)v * g.nu + iu;
             const FxCol cF = g.colF[col];
             const bool famY = g.colB[col].z != 0.f;
             const int m = famY ? j : i;
             const int bb = famY ? i : j;
-            // in-plane weight, from exactly K1's crossing q_b(m)
             const long long qb = cF.qb0 + (long long)m * cF.qb1;
             const int b0 = fx_floor(qb);
             const float fb = fx_frac(qb);
             const float wb = (b0 == bb) ? 1.f - fb : ((b0 + 1 == bb) ? fb : 0.f);
             if (wb == 0.f) continue;
-            // q_z = n*Z + cz for row iv with n = 2*iv - (nv-1); Z > 0 because the
-            // plane lies between source and detector
+            // row iv crosses plane m at q_z = n*Z + cz, n = 2*iv - (nv-1)
             const long long Z = cF.h0 + (long long)m * cF.h1;
-            const float4 cA = g.colA[col];
-            const float Zc = fmaf((float)m, cA.w, cA.z);
-            const float inv = 1.f / (Zc * g.dv);  // detector rows per voxel along z
-            const float hv = inv * 1.0001f + 1e-3f;
-            const float *rcol = rview + iu;
+            const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;  // q_z = 2*iv*Z + zoff
+            // 0 < Z < 2^40 here; converting through a 32-bit integer keeps the FP64 pipe idle
+            const float step = (float)(int)(Z >> 15) * kInv24;            // dq_z per row = 2Z
+            const float inv = 1.f / step;                                 // rows per voxel
+            const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * step;  // estimate only
+            const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
 #pragma unroll
-            for (int q = 0; q < K2_KS; ++q) {
-                const int k = k0 + q;
-                const float ivs = fmaf((float)k - g.cz, inv, g.cv);
-                const int lo = max(0, (int)ceilf(ivs - hv));
-                const int hi = min(g.nv - 1, (int)floorf(ivs + hv));
-                long long qz = (long long)(2 * lo - (g.nv - 1)) * Z + g.cz_fx;
+            for (int q = 0; q < K2_VPL; ++q) {
+                const int k = kbase + K2_LANES * q;
+                // first detector row of voxel k's vertical footprint: the first row
+                // whose crossing lies above k - 1 (estimate, then one exact correction)
+                const float ivs = ((float)k - zoff_f) * inv;
+                int lo = (int)ceilf(ivs - inv);
+                const long long d_fx = 2LL * lo * Z + zoff - ((long long)k << FX_BITS);
+                // q_z(lo) - k to 2^-24 (|q_z(lo) - k| < 2 + step, so d_fx >> 16 fits 32 bits)
+                float d0 = (float)(int)(d_fx >> 16) * kInv24;
+                if (d0 <= -1.f) {
+                    ++lo;
+                    d0 += step;
+                } else if (d0 - step > -1.f) {
+                    --lo;
+                    d0 -= step;
+                }
+                // a window clamped to the zero pads has no real row in it (ntap <= RT_PAD)
+                lo = min(max(lo, -RT_PAD), lo_max);
                 float sz = 0.f;
-                for (int iv = lo; iv <= hi; ++iv) {
-                    const int kz = fx_floor(qz);
-                    const float fz = fx_frac(qz);
-                    const float wz = (kz == k) ? 1.f - fz : ((kz + 1 == k) ? fz : 0.f);
-                    sz = fmaf(wz, __ldg(rcol + (size_t)iv * g.nu), sz);
-                    qz += 2 * Z;
+                for (int t = 0; t < g.ntap; ++t) {
+                    const float d = fmaf((float)t, step, d0);
+                    const float w = fmaxf(0.f, 1.f - fabsf(d));
+                    sz = fmaf(w, __ldg(rcol + lo + t), sz);
                 }
                 acc[q] = fmaf(wb, sz, acc[q]);
             }
         }
     }
+    float *out = a.gzi + ((size_t)j * g.nx + i) * g.nz;
 #pragma unroll
-    for (int q = 0; q < K2_KS; ++q) {
-        const int k = k0 + q;
-        if (k < g.nz) {
-            float *p = a.gout + ((size_t)k * g.ny + j) * g.nx + i;
-            const float val = a.scale * acc[q];
-            *p = a.accumulate ? *p + val : val;
-        }
+    for (int q = 0; q < K2_VPL; ++q) {
+        const int k = kbase + K2_LANES * q;
+        if (k < g.nz) out[k] = a.scale * acc[q];
     }
 }
 
 }  // namespace
 
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
-                               int n_sel, float scale, float *gout, int accumulate,
-                               cudaStream_t st) {
+                               int n_sel, float scale, float *gzi, cudaStream_t st) {
     BpArgs a;
     a.g = g;
     a.rt = rt;
     a.views = views;
     a.n_sel = n_sel;
     a.scale = scale;
-    a.gout = gout;
-    a.accumulate = accumulate;
-    dim3 block(K2_BX, K2_BY);
-    dim3 grid((g.nx + K2_BX - 1) / K2_BX, (g.ny + K2_BY - 1) / K2_BY, (g.nz + K2_KS - 1) / K2_KS);
+    a.gzi = gzi;
+    dim3 block(K2_LANES, K2_WARPS);
+    dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_KSPAN - 1) / K2_KSPAN);
     k2_backproject<<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -2,36 +2,41 @@
 // with the residual and the FP64 objective reduction of Step 2b / Step 2c
 // fused into its epilogue.
 //
-// One thread follows one ray (view s, column iu, row iv) through every plane
-// m of its dominant axis that its bilinear footprint touches.  A block is a
-// 32 x 8 tile of the detector of one view; the grid runs the detector rows
-// slowest, so the blocks resident at one time cover every view of the batch
-// for one band of rows and share a z-slab of the volume in L2.
+// Work decomposition.  A warp follows the 32 rays of 32 consecutive detector
+// rows of one detector column through every plane m of their dominant axis
+// (one lane per ray).  All rays of a column share the in-plane crossing
+// q_b(m) (the detector's v axis is vertical), so the warp reads, per plane,
+// two adjacent rows b0, b0+1 of the z-innermost volume layout over a run of
+// consecutive k: about five 32-byte sectors per load instead of one sector
+// per lane.  Both ray families read the same volume copy with their own
+// plane and in-plane strides.  A block is 8 columns of one view; the grid runs the 32-row
+// bands slowest, so the blocks resident together cover every view of the
+// batch for one band of rows and share a z-slab of the volume in L2.
 //
-// Per-ray constants come from the geometry's column tables (FP64 on the host,
-// rounded once to Q.40 fixed point): q_b(m) = qb0 + m*qb1 and
+// Arithmetic.  Per-ray constants come from the geometry's column tables (FP64
+// on the host, rounded once to Q.40 fixed point): q_b(m) = qb0 + m*qb1 and
 // q_z(m) = n*(h0 + m*h1) + cz.  Stepping from plane to plane adds an integer,
-// so every crossing equals its closed form exactly and the gather
-// backprojector reproduces it bit for bit.  The plane interval [m0, m1] is the
-// exact set of planes on which the crossing lies inside (-1, Nb) x (-1, nz)
-// (an interval, the maps being affine in m), and the padded volume layout
-// supplies the zero border, so the inner loop has no branch.
+// so every crossing equals its closed form exactly.  Each ray's plane interval
+// [m0, m1] is the exact set of planes whose crossing lies inside
+// (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp walks
+// the union of its lanes' intervals, and a lane outside its own interval
+// samples the zero row k = -1 with weight 0.  Interpolation and the ray sum
+// are FP32; the squared residuals are summed in FP64 across threads and
+// blocks in a fixed order.
 #include "fbl_internal.cuh"
 #include "fbl_reduce.cuh"
 
 namespace fbl {
 namespace {
 
-constexpr int K1_BX = 32;
-constexpr int K1_BY = 8;
-constexpr int K1_NT = K1_BX * K1_BY;
+constexpr int K1_ROWS = 32;  // lanes: consecutive detector rows
+constexpr int K1_COLS = 8;   // warps: consecutive detector columns
+constexpr int K1_NT = K1_ROWS * K1_COLS;
 
 struct ProjArgs {
     DevGeom g;
-    const void *padX;
-    PadLayout LX;
-    const void *padY;
-    PadLayout LY;
+    const void *vol;
+    ZLayout L;
     const int32_t *views;
     const void *b;
     const int32_t *b_views;
@@ -68,74 +73,44 @@ struct RayConst {
     }
 };
 
-// Joseph sum of one ray over its planes (without the row weight).
-template <typename TX>
-__device__ __forceinline__ float ray_sum(const RayConst &rc, const TX *__restrict__ vol,
-                                         const PadLayout &L) {
-    float mlo = 0.f, mhi = (float)(L.Na - 1);
+// Exact plane interval of one ray ([m0, m1], empty if m0 > m1).
+__device__ __forceinline__ void plane_range(const RayConst &rc, int Na, int &m0, int &m1) {
+    float mlo = 0.f, mhi = (float)(Na - 1);
     clip_affine(rc.fqb0, rc.fqb1, -1.f, rc.Nb, mlo, mhi);
     clip_affine(fmaf(rc.w, rc.fzc0, rc.cz), rc.w * rc.fzc1, -1.f, rc.Nz, mlo, mhi);
-    if (!(mlo <= mhi + 2.f)) return 0.f;
-    int m0 = max(0, (int)floorf(mlo) - 1);
-    int m1 = min(L.Na - 1, (int)ceilf(mhi) + 1);
-    // exact interval: the crossings are affine in m, so "inside" holds on an interval
-    while (m0 <= m1 && !rc.inside(m0)) ++m0;
-    while (m1 >= m0 && !rc.inside(m1)) --m1;
-    if (m0 > m1) return 0.f;
-    while (m0 > 0 && rc.inside(m0 - 1)) --m0;
-    while (m1 < L.Na - 1 && rc.inside(m1 + 1)) ++m1;
-    const int sK = L.Na * L.pitch;
-    const TX *row = vol + ((size_t)sK + L.PL + (size_t)m0 * L.pitch);  // (b = 0, m = m0, k = 0)
-    long long qb = rc.qb0 + (long long)m0 * rc.qb1;
-    long long qz = rc.qz0 + (long long)m0 * rc.qz1;
-    float acc0 = 0.f, acc1 = 0.f;
-    int m = m0;
-    for (; m + 1 <= m1; m += 2) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int b0 = fx_floor(qb), k0 = fx_floor(qz);
-            const float fb = fx_frac(qb), fz = fx_frac(qz);
-            const TX *p = row + (k0 * sK + b0);
-            const float v00 = ldg_f32(p), v01 = ldg_f32(p + 1);
-            const float v10 = ldg_f32(p + sK), v11 = ldg_f32(p + sK + 1);
-            const float lo = fmaf(fb, v01 - v00, v00);
-            const float hi = fmaf(fb, v11 - v10, v10);
-            const float val = fmaf(fz, hi - lo, lo);
-            if (h == 0) acc0 += val; else acc1 += val;
-            qb += rc.qb1;
-            qz += rc.qz1;
-            row += L.pitch;
-        }
-    }
-    if (m <= m1) {
-        const int b0 = fx_floor(qb), k0 = fx_floor(qz);
-        const float fb = fx_frac(qb), fz = fx_frac(qz);
-        const TX *p = row + (k0 * sK + b0);
-        const float v00 = ldg_f32(p), v01 = ldg_f32(p + 1);
-        const float v10 = ldg_f32(p + sK), v11 = ldg_f32(p + sK + 1);
-        const float lo = fmaf(fb, v01 - v00, v00);
-        const float hi = fmaf(fb, v11 - v10, v10);
-        acc0 += fmaf(fz, hi - lo, lo);
-    }
-    return acc0 + acc1;
+    m0 = 1;
+    m1 = 0;
+    if (!(mlo <= mhi + 2.f)) return;
+    int a = max(0, (int)floorf(mlo) - 1);
+    int c = min(Na - 1, (int)ceilf(mhi) + 1);
+    while (a <= c && !rc.inside(a)) ++a;
+    while (c >= a && !rc.inside(c)) --c;
+    if (a > c) return;
+    while (a > 0 && rc.inside(a - 1)) --a;
+    while (c < Na - 1 && rc.inside(c + 1)) ++c;
+    m0 = a;
+    m1 = c;
 }
 
 template <typename TX, typename TB, typename TO, int MODE>
 __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
     const DevGeom &g = a.g;
-    const int iu = blockIdx.x * K1_BX + threadIdx.x;
+    const int lane = threadIdx.x;
+    const int iu = blockIdx.x * K1_COLS + threadIdx.y;  // uniform over the warp
     const int s = blockIdx.y;
-    const int iv = blockIdx.z * K1_BY + threadIdx.y;
+    const int iv = blockIdx.z * K1_ROWS + lane;
     float r2 = 0.f;
-    if (iu < g.nu && iv < g.nv) {
+    if (iu < g.nu) {
         const int v = a.views[s];
         const size_t col = (size_t)v * g.nu + iu;
         const float4 cA = g.colA[col];
         const float4 cB = g.colB[col];
         const FxCol cF = g.colF[col];
         const bool famY = cB.z != 0.f;
-        const PadLayout &L = famY ? a.LY : a.LX;
-        const TX *vol = (const TX *)(famY ? a.padY : a.padX);
+        const ZLayout &L = a.L;
+        const int Na = famY ? g.ny : g.nx;  // planes along the dominant axis
+        const int Nb = famY ? g.nx : g.ny;  // in-plane extent
+        const TX *vol = (const TX *)a.vol;
         const int n = 2 * iv - (g.nv - 1);  // w = n * dv / 2
         RayConst rc;
         rc.fqb0 = cA.x;
@@ -144,32 +119,68 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
         rc.fzc1 = cA.w;
         rc.w = (float)n * (0.5f * g.dv);
         rc.cz = g.cz;
-        rc.Nb = (float)L.Nb;
+        rc.Nb = (float)Nb;
         rc.Nz = (float)g.nz;
         rc.qb0 = cF.qb0;
         rc.qb1 = cF.qb1;
         rc.qz0 = (long long)n * cF.h0 + g.cz_fx;
         rc.qz1 = (long long)n * cF.h1;
-        rc.hi_b = (long long)L.Nb << FX_BITS;
+        rc.hi_b = (long long)Nb << FX_BITS;
         rc.hi_z = (long long)g.nz << FX_BITS;
-        const float sum = ray_sum<TX>(rc, vol, L);
-        const float W = cB.x * sqrtf(fmaf(rc.w, rc.w, cB.y));
-        const float ax = W * sum;
-        const size_t o = ((size_t)s * g.nv + iv) * g.nu + iu;
-        if (MODE == PROJ_STORE) {
-            ((TO *)a.out)[o] = from_f32<TO>(ax);
-        } else {
-            const int bv = a.b_views ? a.b_views[s] : s;
-            const float bval = ldg_f32((const TB *)a.b + ((size_t)bv * g.nv + iv) * g.nu + iu);
-            const float r = ax - bval;
-            if (MODE == PROJ_RESID) ((float *)a.out)[o] = W * r;
-            r2 = r * r;
+        int m0 = 1, m1 = 0;
+        if (iv < g.nv) plane_range(rc, Na, m0, m1);
+        const bool has = m0 <= m1;
+        const int own0 = has ? m0 : (1 << 30);
+        const int own1 = has ? m1 : -1;
+        const int mu0 = __reduce_min_sync(0xffffffffu, own0);
+        const int mu1 = __reduce_max_sync(0xffffffffu, own1);
+        float acc0 = 0.f, acc1 = 0.f;
+        if (mu0 <= mu1) {
+            const int ps = L.plane_stride(famY);  // next plane
+            const int bs = L.inplane_stride(famY);  // next in-plane voxel
+            // element (b, m, k) = vol + [PL + (m+1)*ps + (b+1)*bs + k]
+            int off_m = L.PL + (mu0 + 1) * ps + bs;
+            long long qb = rc.qb0 + (long long)mu0 * rc.qb1;
+            long long qz = rc.qz0 + (long long)mu0 * rc.qz1;
+#pragma unroll 2
+            for (int m = mu0; m <= mu1; ++m) {
+                const bool in = (m >= own0) & (m <= own1);
+                const int b0 = fx_floor(qb);
+                const float fb = fx_frac(qb);
+                const int k0 = in ? fx_floor(qz) : -1;
+                const float fz = in ? fx_frac(qz) : 0.f;
+                const TX *p = vol + (off_m + b0 * bs + k0);
+                const float v00 = ldg_f32(p), v10 = ldg_f32(p + 1);
+                const float v01 = ldg_f32(p + bs), v11 = ldg_f32(p + bs + 1);
+                const float lo = fmaf(fb, v01 - v00, v00);
+                const float hi = fmaf(fb, v11 - v10, v10);
+                const float val = fmaf(fz, hi - lo, lo);
+                if (m & 1) acc1 += val; else acc0 += val;
+                qb += rc.qb1;
+                qz += rc.qz1;
+                off_m += ps;
+            }
+        }
+        if (iv < g.nv) {
+            const float sum = acc0 + acc1;
+            const float W = cB.x * sqrtf(fmaf(rc.w, rc.w, cB.y));
+            const float ax = W * sum;
+            if (MODE == PROJ_STORE) {
+                ((TO *)a.out)[((size_t)s * g.nv + iv) * g.nu + iu] = from_f32<TO>(ax);
+            } else {
+                const int bv = a.b_views ? a.b_views[s] : s;
+                const float bval = ldg_f32((const TB *)a.b + ((size_t)bv * g.nv + iv) * g.nu + iu);
+                const float r = ax - bval;
+                if (MODE == PROJ_RESID)
+                    ((float *)a.out)[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = W * r;
+                r2 = r * r;
+            }
         }
     }
     if (MODE != PROJ_STORE) {
-        float v[1] = {r2};
+        float vv[1] = {r2};
         double out[1];
-        block_sum_f64<K1_NT, 1>(v, out);
+        block_sum_f64<K1_NT, 1>(vv, out);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             a.partials[blk] = out[0];
@@ -177,26 +188,39 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
     }
 }
 
-// rt[s][iv][iu] = W(ray) * y[s][iv][iu]
+// rt[s][iu][RT_PAD + iv] = W(ray) * y[s][iv][iu], through a 32 x 32 shared tile
+// (reads along iu, writes along iv).
 template <typename TY>
-__global__ void k_weight(const DevGeom g, const TY *__restrict__ y, const int32_t *views,
-                         float *__restrict__ rt) {
-    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iv = blockIdx.y;
+__global__ void __launch_bounds__(256) k_weight(const DevGeom g, const TY *__restrict__ y,
+                                                const int32_t *views, float *__restrict__ rt) {
+    __shared__ float tile[32][33];
     const int s = blockIdx.z;
-    if (iu >= g.nu) return;
+    const int iu0 = blockIdx.x * 32, iv0 = blockIdx.y * 32;
     const int v = views[s];
-    const float4 cB = g.colB[(size_t)v * g.nu + iu];
-    const float w = (float)(2 * iv - (g.nv - 1)) * (0.5f * g.dv);
-    const float W = cB.x * sqrtf(fmaf(w, w, cB.y));
-    const size_t o = ((size_t)s * g.nv + iv) * g.nu + iu;
-    rt[o] = W * to_f32(y[o]);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int iv = iv0 + ty + 8 * r, iu = iu0 + tx;
+        if (iu < g.nu && iv < g.nv) {
+            const float4 cB = g.colB[(size_t)v * g.nu + iu];
+            const float w = (float)(2 * iv - (g.nv - 1)) * (0.5f * g.dv);
+            const float W = cB.x * sqrtf(fmaf(w, w, cB.y));
+            tile[ty + 8 * r][tx] = W * to_f32(y[((size_t)s * g.nv + iv) * g.nu + iu]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int iu = iu0 + ty + 8 * r, iv = iv0 + tx;
+        if (iu < g.nu && iv < g.nv)
+            rt[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = tile[tx][ty + 8 * r];
+    }
 }
 
 template <typename TX, typename TB, typename TO, int MODE>
 cudaError_t launch_t(const ProjArgs &a, int n_sel, cudaStream_t st) {
-    dim3 block(K1_BX, K1_BY);
-    dim3 grid((a.g.nu + K1_BX - 1) / K1_BX, n_sel, (a.g.nv + K1_BY - 1) / K1_BY);
+    dim3 block(K1_ROWS, K1_COLS);
+    dim3 grid((a.g.nu + K1_COLS - 1) / K1_COLS, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
     k1_project<TX, TB, TO, MODE><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -226,24 +250,21 @@ cudaError_t launch_bdt(int mode, int b_dtype, int out_dtype, const ProjArgs &a, 
 }  // namespace
 
 int project_num_partials(const DevGeom &g, int n_sel) {
-    return ((g.nu + K1_BX - 1) / K1_BX) * n_sel * ((g.nv + K1_BY - 1) / K1_BY);
+    return ((g.nu + K1_COLS - 1) / K1_COLS) * n_sel * ((g.nv + K1_ROWS - 1) / K1_ROWS);
 }
 
-cudaError_t launch_project(int mode, const DevGeom &g, const void *padX, PadLayout LX,
-                           const void *padY, PadLayout LY, int x_dtype, const int32_t *views,
-                           int n_sel, const void *b, int b_dtype, const int32_t *b_views,
-                           void *out, int out_dtype, double *partials, int *n_partials,
-                           cudaStream_t st) {
+cudaError_t launch_project(int mode, const DevGeom &g, const void *vol, ZLayout L, int x_dtype,
+                           const int32_t *views, int n_sel, const void *b, int b_dtype,
+                           const int32_t *b_views, void *out, int out_dtype, double *partials,
+                           int *n_partials, cudaStream_t st) {
     if (n_sel <= 0) {
         if (n_partials) *n_partials = 0;
         return cudaSuccess;
     }
     ProjArgs a;
     a.g = g;
-    a.padX = padX;
-    a.LX = LX;
-    a.padY = padY;
-    a.LY = LY;
+    a.vol = vol;
+    a.L = L;
     a.views = views;
     a.b = b;
     a.b_views = b_views;
@@ -260,8 +281,8 @@ cudaError_t launch_project(int mode, const DevGeom &g, const void *padX, PadLayo
 cudaError_t launch_weight(const DevGeom &g, const void *y, int y_dtype, const int32_t *views,
                           int n_sel, float *rt, cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
-    dim3 block(128);
-    dim3 grid((g.nu + 127) / 128, g.nv, n_sel);
+    dim3 block(32, 8);
+    dim3 grid((g.nu + 31) / 32, (g.nv + 31) / 32, n_sel);
     switch (y_dtype) {
         case FBL_BF16: k_weight<<<grid, block, 0, st>>>(g, (const __nv_bfloat16 *)y, views, rt); break;
         case FBL_F16: k_weight<<<grid, block, 0, st>>>(g, (const __half *)y, views, rt); break;

@@ -3,12 +3,12 @@
 // R = mu||.||_1 + indicator{x >= 0} (eq. (2.1)), fused with the reductions the
 // test (2.3) needs: g^T (x_bar - x), ||x_bar - x||^2 (and ||x_bar||_1 for the
 // objective F), all taken over the stored (rounded) x_bar.  Memory-bound:
-// per voxel it reads x and g once and writes x_bar in the two padded layouts
-// the projector reads (the transposed one through a shared-memory tile).
+// per voxel it reads x and g once and writes x_bar once, in the z-innermost
+// layout the projector reads; every stream is contiguous along z.
 //
-// Also here: the pack kernel that builds the two padded layouts from a
-// caller's volume, the flat prox for the public prox_reduce call, and the
-// fixed-order FP64 reduction of per-block partial sums.
+// Also here: the kernels that convert between the caller's [nz][ny][nx]
+// volumes and the library's z-innermost layouts, the flat prox for the public
+// prox_reduce call, and the fixed-order FP64 reduction of per-block sums.
 #include "fbl_internal.cuh"
 #include "fbl_reduce.cuh"
 
@@ -19,75 +19,109 @@ constexpr int TB = 32;        // tile edge
 constexpr int TR = 8;         // tile rows per pass
 constexpr int P_NT = TB * TR; // threads per block
 
-// Natural [nz][ny][nx] volume -> padded Y layout (same orientation) and
-// padded X layout (i and j swapped inside each z-slice).
+// Natural [nz][ny][nx] volume -> the library layout.  For each j, a
+// 32 x 32 (k, i) tile is read along i and written along k.
 template <typename T>
-__global__ void __launch_bounds__(P_NT) k_pack(const T *__restrict__ x, int nx, int ny, int nz,
-                                               T *__restrict__ padY, PadLayout LY,
-                                               T *__restrict__ padX, PadLayout LX) {
-    __shared__ T tile[TB][TB + 1];
-    const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB, k = blockIdx.z;
+__global__ void __launch_bounds__(P_NT) k_pack(const T *__restrict__ x, T *__restrict__ vol,
+                                               ZLayout L) {
+    __shared__ T tile[TB][TB + 1];  // [k][i]
+    const int i0 = blockIdx.x * TB, k0 = blockIdx.y * TB, j = blockIdx.z;
     const int tx = threadIdx.x, ty = threadIdx.y;
 #pragma unroll
     for (int r = 0; r < TB / TR; ++r) {
-        const int j = j0 + ty + TR * r, i = i0 + tx;
-        if (i < nx && j < ny) {
-            const T v = x[((size_t)k * ny + j) * nx + i];
-            padY[LY.index(i, j, k)] = v;
-            tile[ty + TR * r][tx] = v;
-        }
+        const int k = k0 + ty + TR * r, i = i0 + tx;
+        if (i < L.nx && k < L.nz) tile[ty + TR * r][tx] = x[((size_t)k * L.ny + j) * L.nx + i];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < TB / TR; ++r) {
-        const int i = i0 + ty + TR * r, j = j0 + tx;
-        if (i < nx && j < ny) padX[LX.index(j, i, k)] = tile[tx][ty + TR * r];
+        const int i = i0 + ty + TR * r, k = k0 + tx;
+        if (i < L.nx && k < L.nz) vol[L.index(i, j, k)] = tile[tx][ty + TR * r];
     }
 }
 
+// Library layout -> natural [nz][ny][nx].
 template <typename T>
-__global__ void __launch_bounds__(P_NT) k_prox_padded(const T *__restrict__ padY, PadLayout LY,
-                                                      const float *__restrict__ gr, float alpha,
-                                                      float amu, T *__restrict__ trialY,
-                                                      T *__restrict__ trialX, PadLayout LX,
-                                                      int nx, int ny, int nz,
-                                                      double *__restrict__ partials) {
-    __shared__ T tile[TB][TB + 1];
-    const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB, k = blockIdx.z;
+__global__ void __launch_bounds__(P_NT) k_unpack(const T *__restrict__ vol, ZLayout L,
+                                                 T *__restrict__ x) {
+    __shared__ T tile[TB][TB + 1];  // [i][k]
+    const int i0 = blockIdx.x * TB, k0 = blockIdx.y * TB, j = blockIdx.z;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    float sums[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int r = 0; r < TB / TR; ++r) {
-        const int j = j0 + ty + TR * r, i = i0 + tx;
-        if (i < nx && j < ny) {
-            const int64_t py = LY.index(i, j, k);
-            const float x = to_f32(padY[py]);
-            const float gg = gr[((size_t)k * ny + j) * nx + i];
+        const int i = i0 + ty + TR * r, k = k0 + tx;
+        if (i < L.nx && k < L.nz) tile[ty + TR * r][tx] = vol[L.index(i, j, k)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < TB / TR; ++r) {
+        const int k = k0 + ty + TR * r, i = i0 + tx;
+        if (i < L.nx && k < L.nz) x[((size_t)k * L.ny + j) * L.nx + i] = tile[tx][ty + TR * r];
+    }
+}
+
+// Gradient order [j][i][k] -> natural [nz][ny][nx] (= or +=).
+__global__ void __launch_bounds__(P_NT) k_zi_to_natural(const float *__restrict__ gzi,
+                                                        float *__restrict__ x, int nx, int ny,
+                                                        int nz, int accumulate) {
+    __shared__ float tile[TB][TB + 1];  // [i][k]
+    const int i0 = blockIdx.x * TB, k0 = blockIdx.y * TB, j = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int r = 0; r < TB / TR; ++r) {
+        const int i = i0 + ty + TR * r, k = k0 + tx;
+        if (i < nx && k < nz) tile[ty + TR * r][tx] = gzi[((size_t)j * nx + i) * nz + k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < TB / TR; ++r) {
+        const int k = k0 + ty + TR * r, i = i0 + tx;
+        if (i < nx && k < nz) {
+            float *p = x + ((size_t)k * ny + j) * nx + i;
+            const float v = tile[tx][ty + TR * r];
+            *p = accumulate ? *p + v : v;
+        }
+    }
+}
+
+// Prox + reductions, streaming along z: a block owns 4 (i, j) rows of the
+// z-innermost volumes; every read and write is contiguous along k.
+constexpr int PZ_TX = 64;
+constexpr int PZ_TY = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi(const T *__restrict__ vol, ZLayout L,
+                                                          const float *__restrict__ gzi, float alpha,
+                                                          float amu, T *__restrict__ trial,
+                                                          double *__restrict__ partials) {
+    const int row = blockIdx.x * PZ_TY + threadIdx.y;
+    float sums[3] = {0.f, 0.f, 0.f};
+    if (row < L.nx * L.ny) {
+        const int j = row / L.nx, i = row - j * L.nx;
+        const int64_t base = L.index(i, j, 0);
+        const T *src = vol + base;
+        T *dst = trial + base;
+        const float *gr = gzi + (size_t)row * L.nz;
+        for (int k = threadIdx.x; k < L.nz; k += PZ_TX) {
+            const float x = to_f32(src[k]);
+            const float gg = gr[k];
             const float xb = fmaxf(fmaf(-alpha, gg, x) - amu, 0.f);
             const T xs = from_f32<T>(xb);
             const float xr = to_f32(xs);
-            trialY[py] = xs;
-            tile[ty + TR * r][tx] = xs;
+            dst[k] = xs;
             const float d = xr - x;
             sums[0] = fmaf(gg, d, sums[0]);
             sums[1] = fmaf(d, d, sums[1]);
             sums[2] += xr;
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < TB / TR; ++r) {
-        const int i = i0 + ty + TR * r, j = j0 + tx;
-        if (i < nx && j < ny) trialX[LX.index(j, i, k)] = tile[tx][ty + TR * r];
-    }
     double out[3];
-    block_sum_f64<P_NT, 3>(sums, out);
-    if (tx == 0 && ty == 0) {
-        const size_t nblk = (size_t)gridDim.x * gridDim.y * gridDim.z;
-        const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[blk] = out[0];
-        partials[nblk + blk] = out[1];
-        partials[2 * nblk + blk] = out[2];
+    block_sum_f64<PZ_TX * PZ_TY, 3>(sums, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const size_t nblk = gridDim.x;
+        partials[blockIdx.x] = out[0];
+        partials[nblk + blockIdx.x] = out[1];
+        partials[2 * nblk + blockIdx.x] = out[2];
     }
 }
 
@@ -149,53 +183,63 @@ __global__ void __launch_bounds__(R_NT) k_reduce(const double *__restrict__ part
 
 }  // namespace
 
-cudaError_t launch_pack(const void *x, int x_dtype, int nx, int ny, int nz, void *padY,
-                        PadLayout LY, void *padX, PadLayout LX, cudaStream_t st) {
+cudaError_t launch_pack(const void *x, int x_dtype, void *vol, ZLayout L, cudaStream_t st) {
     dim3 block(TB, TR);
-    dim3 grid((nx + TB - 1) / TB, (ny + TB - 1) / TB, nz);
+    dim3 grid((L.nx + TB - 1) / TB, (L.nz + TB - 1) / TB, L.ny);
     switch (x_dtype) {
         case FBL_BF16:
-            k_pack<<<grid, block, 0, st>>>((const __nv_bfloat16 *)x, nx, ny, nz,
-                                           (__nv_bfloat16 *)padY, LY, (__nv_bfloat16 *)padX, LX);
+            k_pack<<<grid, block, 0, st>>>((const __nv_bfloat16 *)x, (__nv_bfloat16 *)vol, L);
             break;
-        case FBL_F16:
-            k_pack<<<grid, block, 0, st>>>((const __half *)x, nx, ny, nz, (__half *)padY, LY,
-                                           (__half *)padX, LX);
-            break;
-        default:
-            k_pack<<<grid, block, 0, st>>>((const float *)x, nx, ny, nz, (float *)padY, LY,
-                                           (float *)padX, LX);
-            break;
+        case FBL_F16: k_pack<<<grid, block, 0, st>>>((const __half *)x, (__half *)vol, L); break;
+        default: k_pack<<<grid, block, 0, st>>>((const float *)x, (float *)vol, L); break;
     }
     return cudaGetLastError();
 }
 
-int prox_padded_num_partials(int nx, int ny, int nz) {
-    return ((nx + TB - 1) / TB) * ((ny + TB - 1) / TB) * nz;
-}
-
-cudaError_t launch_prox_padded(const void *padY, PadLayout LY, const float *gr, float alpha,
-                               float amu, void *trialY, void *trialX, PadLayout LX, int dtype,
-                               int nx, int ny, int nz, double *partials, int *n_partials,
-                               cudaStream_t st) {
+cudaError_t launch_unpack(const void *vol, ZLayout L, int dtype, void *x, cudaStream_t st) {
     dim3 block(TB, TR);
-    dim3 grid((nx + TB - 1) / TB, (ny + TB - 1) / TB, nz);
-    if (n_partials) *n_partials = prox_padded_num_partials(nx, ny, nz);
+    dim3 grid((L.nx + TB - 1) / TB, (L.nz + TB - 1) / TB, L.ny);
     switch (dtype) {
         case FBL_BF16:
-            k_prox_padded<<<grid, block, 0, st>>>((const __nv_bfloat16 *)padY, LY, gr, alpha, amu,
-                                                  (__nv_bfloat16 *)trialY, (__nv_bfloat16 *)trialX,
-                                                  LX, nx, ny, nz, partials);
+            k_unpack<<<grid, block, 0, st>>>((const __nv_bfloat16 *)vol, L, (__nv_bfloat16 *)x);
+            break;
+        case FBL_F16: k_unpack<<<grid, block, 0, st>>>((const __half *)vol, L, (__half *)x); break;
+        default: k_unpack<<<grid, block, 0, st>>>((const float *)vol, L, (float *)x); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zi_to_natural(const float *gzi, float *x, int nx, int ny, int nz, int accumulate,
+                                 cudaStream_t st) {
+    dim3 block(TB, TR);
+    dim3 grid((nx + TB - 1) / TB, (nz + TB - 1) / TB, ny);
+    k_zi_to_natural<<<grid, block, 0, st>>>(gzi, x, nx, ny, nz, accumulate);
+    return cudaGetLastError();
+}
+
+int prox_zi_num_partials(int nx, int ny, int nz) {
+    (void)nz;
+    return (nx * ny + PZ_TY - 1) / PZ_TY;
+}
+
+cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu,
+                           void *trial, int dtype, double *partials, int *n_partials,
+                           cudaStream_t st) {
+    const int nb = prox_zi_num_partials(L.nx, L.ny, L.nz);
+    if (n_partials) *n_partials = nb;
+    dim3 block(PZ_TX, PZ_TY);
+    switch (dtype) {
+        case FBL_BF16:
+            k_prox_zi<<<nb, block, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, alpha, amu,
+                                            (__nv_bfloat16 *)trial, partials);
             break;
         case FBL_F16:
-            k_prox_padded<<<grid, block, 0, st>>>((const __half *)padY, LY, gr, alpha, amu,
-                                                  (__half *)trialY, (__half *)trialX, LX, nx, ny,
-                                                  nz, partials);
+            k_prox_zi<<<nb, block, 0, st>>>((const __half *)vol, L, gzi, alpha, amu, (__half *)trial,
+                                            partials);
             break;
         default:
-            k_prox_padded<<<grid, block, 0, st>>>((const float *)padY, LY, gr, alpha, amu,
-                                                  (float *)trialY, (float *)trialX, LX, nx, ny, nz,
-                                                  partials);
+            k_prox_zi<<<nb, block, 0, st>>>((const float *)vol, L, gzi, alpha, amu, (float *)trial,
+                                            partials);
             break;
     }
     return cudaGetLastError();
@@ -249,13 +293,6 @@ cudaError_t launch_reduce(const double *partials, int n, int stride, int ncomp, 
                           cudaStream_t st) {
     k_reduce<<<ncomp, R_NT, 0, st>>>(partials, n, stride, out);
     return cudaGetLastError();
-}
-
-cudaError_t copy_unpad(const void *padY, PadLayout LY, int esize, void *x, int nx, int ny, int nz,
-                       cudaStream_t st) {
-    const char *src = (const char *)padY + LY.index(0, 0, 0) * esize;
-    return cudaMemcpy2DAsync(x, (size_t)nx * esize, src, (size_t)LY.pitch * esize,
-                             (size_t)nx * esize, (size_t)ny * nz, cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace fbl

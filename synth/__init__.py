@@ -96,6 +96,9 @@ WORKLOADS: Dict[str, Workload] = {
                        N0=20, epochs=20, seed_phantom=1002, seed_noise=2002, seed_batches=3002),
     "c3_512": Workload("c3_512", _cube(512, 720, 768), 100, 0, 0.02, "gaussian", 0.01, 0.0,
                        N0=40, epochs=10, seed_phantom=1003, seed_noise=2003, seed_batches=3003),
+    # a profiling-sized case: volume larger than L2, a few GB on the device in all
+    "p384": Workload("p384", _cube(384, 120, 576), 40, 0, 0.0, "gaussian", 0.01, 0.0,
+                     N0=20, epochs=2, seed_phantom=1009, seed_noise=2009, seed_batches=3009),
     "c5b_1024": Workload("c5b_1024", _cube(1024, 1440, 1536), 100, 0, 0.0, "gaussian", 0.01,
                          0.0, N0=60, epochs=10, seed_phantom=1005, seed_noise=2005,
                          seed_batches=3005),
