@@ -8,15 +8,16 @@
 // detector column, wz from the vertical crossing q_z(m) of its row.
 //
 // Work decomposition.  A warp owns 128 voxels of one (i, j) column along z
-// (lane l holds k = k0 + l + 32q, q < 4).  Everything that depends only on
+// (lane l holds the four consecutive voxels k0 + 4l .. k0 + 4l + 3).  Everything that depends only on
 // (i, j) and the view -- the candidate columns within hwu of the voxel
 // column's projection, each column's family, plane m, exact in-plane weight
 // wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
 // over the warp.  Per voxel, the detector rows that can reach it lie among the
-// ntap rows starting at the first row of its vertical footprint; the offset
-// q_z - k of the first is taken exactly from the Q.40 crossing and the next
-// ones follow by the exact per-row step, so wz = max(0, 1 - |q_z - k|) is
-// accurate to a few 1e-7.  The residual arrives transposed and zero-padded
+// ntap rows starting at the first row of its vertical footprint.  For a
+// lane's first voxel the offset q_z - k of that row is taken exactly from the
+// Q.40 crossing; the next rows follow by the per-row step, and the next voxel
+// by subtracting one and dropping the rows that fell below its footprint, so
+// wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  The residual arrives transposed and zero-padded
 // (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
 // lanes' row reads are contiguous and need no bounds test.  The gradient is
 // written in z-innermost order [j][i][k], coalesced.
@@ -39,12 +40,13 @@ struct BpArgs {
     float *gzi;
 };
 
+template <int NTAP>
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
     const DevGeom &g = a.g;
     const int lane = threadIdx.x;
     const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
     const int j = blockIdx.y;
-    const int kbase = blockIdx.z * K2_KSPAN + lane;
+    const int kfirst = blockIdx.z * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+3
     if (i >= g.nx) return;
     float acc[K2_VPL];
 #pragma unroll
@@ -52,7 +54,8 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
     const float xc = ((float)i - g.cx) * g.vx;
     const float yc = ((float)j - g.cy) * g.vy;
     const int rp = rt_pitch(g.nv);
-    const int lo_max = g.nv + RT_PAD - g.ntap;  // last first-row whose taps stay in the pad
+    const int lo_max = g.nv + RT_PAD - NTAP;  // last first-row whose taps stay in the pad
+    const long long kfirst_fx = (long long)kfirst << FX_BITS;
     constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
     for (int s = 0; s < a.n_sel; ++s) {
         const int v = a.views[s];
@@ -73,47 +76,48 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
             const float fb = fx_frac(qb);
             const float wb = (b0 == bb) ? 1.f - fb : ((b0 + 1 == bb) ? fb : 0.f);
             if (wb == 0.f) continue;
-            // row iv crosses plane m at q_z = n*Z + cz, n = 2*iv - (nv-1)
+            // row iv crosses plane m at q_z = 2*iv*Z + zoff (Q.40), 0 < Z < 2^40
             const long long Z = cF.h0 + (long long)m * cF.h1;
-            const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;  // q_z = 2*iv*Z + zoff
-            // 0 < Z < 2^40 here; converting through a 32-bit integer keeps the FP64 pipe idle
-            const float step = (float)(int)(Z >> 15) * kInv24;            // dq_z per row = 2Z
-            const float inv = 1.f / step;                                 // rows per voxel
-            const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * step;  // estimate only
+            const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;
+            const float step = (float)(int)(Z >> 15) * kInv24;  // dq_z per row = 2Z (32-bit path)
+            const float inv = 1.f / step;                       // rows per voxel
+            const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * step;
+            // first row whose crossing lies above kfirst - 1: estimate, then one exact correction
+            int lo = (int)ceilf(((float)kfirst - zoff_f) * inv - inv);
+            const long long d_fx = 2LL * lo * Z + zoff - kfirst_fx;
+            float d0 = (float)(int)(d_fx >> 16) * kInv24;  // q_z(lo) - kfirst (|.| < 2 + step)
+            if (d0 <= -1.f) {
+                ++lo;
+                d0 += step;
+            } else if (d0 - step > -1.f) {
+                --lo;
+                d0 -= step;
+            }
             const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
 #pragma unroll
             for (int q = 0; q < K2_VPL; ++q) {
-                const int k = kbase + K2_LANES * q;
-                // first detector row of voxel k's vertical footprint: the first row
-                // whose crossing lies above k - 1 (estimate, then one exact correction)
-                const float ivs = ((float)k - zoff_f) * inv;
-                int lo = (int)ceilf(ivs - inv);
-                const long long d_fx = 2LL * lo * Z + zoff - ((long long)k << FX_BITS);
-                // q_z(lo) - k to 2^-24 (|q_z(lo) - k| < 2 + step, so d_fx >> 16 fits 32 bits)
-                float d0 = (float)(int)(d_fx >> 16) * kInv24;
-                if (d0 <= -1.f) {
-                    ++lo;
-                    d0 += step;
-                } else if (d0 - step > -1.f) {
-                    --lo;
-                    d0 -= step;
-                }
-                // a window clamped to the zero pads has no real row in it (ntap <= RT_PAD)
-                lo = min(max(lo, -RT_PAD), lo_max);
+                // a window clamped into the zero pads holds no real row (ntap <= RT_PAD)
+                const float *r = rcol + min(max(lo, -RT_PAD), lo_max);
                 float sz = 0.f;
-                for (int t = 0; t < g.ntap; ++t) {
+#pragma unroll
+                for (int t = 0; t < NTAP; ++t) {
                     const float d = fmaf((float)t, step, d0);
-                    const float w = fmaxf(0.f, 1.f - fabsf(d));
-                    sz = fmaf(w, __ldg(rcol + lo + t), sz);
+                    sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(r + t), sz);
                 }
                 acc[q] = fmaf(wb, sz, acc[q]);
+                // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
+                d0 -= 1.f;
+                while (d0 <= -1.f) {
+                    ++lo;
+                    d0 += step;
+                }
             }
         }
     }
     float *out = a.gzi + ((size_t)j * g.nx + i) * g.nz;
 #pragma unroll
     for (int q = 0; q < K2_VPL; ++q) {
-        const int k = kbase + K2_LANES * q;
+        const int k = kfirst + q;
         if (k < g.nz) out[k] = a.scale * acc[q];
     }
 }
@@ -131,7 +135,16 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
     a.gzi = gzi;
     dim3 block(K2_LANES, K2_WARPS);
     dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_KSPAN - 1) / K2_KSPAN);
-    k2_backproject<<<grid, block, 0, st>>>(a);
+    switch (g.ntap) {  // rows per voxel and column, fixed per geometry (<= RT_PAD)
+        case 1: k2_backproject<1><<<grid, block, 0, st>>>(a); break;
+        case 2: k2_backproject<2><<<grid, block, 0, st>>>(a); break;
+        case 3: k2_backproject<3><<<grid, block, 0, st>>>(a); break;
+        case 4: k2_backproject<4><<<grid, block, 0, st>>>(a); break;
+        case 5: k2_backproject<5><<<grid, block, 0, st>>>(a); break;
+        case 6: k2_backproject<6><<<grid, block, 0, st>>>(a); break;
+        case 7: k2_backproject<7><<<grid, block, 0, st>>>(a); break;
+        default: k2_backproject<8><<<grid, block, 0, st>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 //
 // Work decomposition.  A warp follows the 32 rays of 32 consecutive detector
 // rows of one detector column through every plane m of their dominant axis
-// (one lane per ray).  All rays of a column share the in-plane crossing
+// (one ray per lane).  All rays of a column share the in-plane crossing
 // q_b(m) (the detector's v axis is vertical), so the warp reads, per plane,
 // two adjacent rows b0, b0+1 of the z-innermost volume layout over a run of
 // consecutive k: about five 32-byte sectors per load instead of one sector
@@ -19,8 +19,9 @@
 // so every crossing equals its closed form exactly.  Each ray's plane interval
 // [m0, m1] is the exact set of planes whose crossing lies inside
 // (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp walks
-// the union of its lanes' intervals, and a lane outside its own interval
-// samples the zero row k = -1 with weight 0.  Interpolation and the ray sum
+// the union of its rays' intervals -- without per-sample masks where they all
+// overlap, and with masks at the two ends, where a ray outside its own
+// interval samples the zero row k = -1 with weight 0.  Interpolation and the ray sum
 // are FP32; the squared residuals are summed in FP64 across threads and
 // blocks in a fixed order.
 #include "fbl_internal.cuh"
@@ -29,9 +30,9 @@
 namespace fbl {
 namespace {
 
-constexpr int K1_ROWS = 32;  // lanes: consecutive detector rows
+constexpr int K1_ROWS = 32;  // detector rows per warp: one ray per lane
 constexpr int K1_COLS = 8;   // warps: consecutive detector columns
-constexpr int K1_NT = K1_ROWS * K1_COLS;
+constexpr int K1_NT = 32 * K1_COLS;
 
 struct ProjArgs {
     DevGeom g;
@@ -92,6 +93,79 @@ __device__ __forceinline__ void plane_range(const RayConst &rc, int Na, int &m0,
     m1 = c;
 }
 
+// Plane loop over [m_begin, m_end] for a lane's ray.  MASKED: outside its own
+// interval [o0, o1] the ray samples the zero row k = -1 with weight 0.
+template <bool MASKED, typename TX>
+__device__ __forceinline__ float plane_loop(const TX *__restrict__ vol, int m_begin, int m_end,
+                                            int ps, int bs, int base, const RayConst &rc, int o0,
+                                            int o1) {
+    long long qb = rc.qb0 + (long long)m_begin * rc.qb1;
+    long long qz = rc.qz0 + (long long)m_begin * rc.qz1;
+    int off = base + m_begin * ps;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll 2
+    for (int m = m_begin; m <= m_end; ++m) {
+        const int b0 = fx_floor(qb);
+        const float fb = fx_frac(qb);
+        int k0 = fx_floor(qz);
+        float fz = fx_frac(qz);
+        if (MASKED) {
+            const bool in = (m >= o0) & (m <= o1);
+            k0 = in ? k0 : -1;
+            fz = in ? fz : 0.f;
+        }
+        const TX *p = vol + (off + b0 * bs + k0);
+        const float v00 = ldg_f32(p), v10 = ldg_f32(p + 1);
+        const float v01 = ldg_f32(p + bs), v11 = ldg_f32(p + bs + 1);
+        const float lo = fmaf(fb, v01 - v00, v00);
+        const float hi = fmaf(fb, v11 - v10, v10);
+        const float val = fmaf(fz, hi - lo, lo);
+        if (m & 1) s1 += val; else s0 += val;
+        qb += rc.qb1;
+        qz += rc.qz1;
+        off += ps;
+    }
+    return s0 + s1;
+}
+
+template <typename TX>
+__device__ __forceinline__ void make_ray(const DevGeom &g, const float4 &cA, const FxCol &cF, int Nb,
+                                         int iv, RayConst &rc) {
+    const int n = 2 * iv - (g.nv - 1);  // w = n * dv / 2
+    rc.fqb0 = cA.x;
+    rc.fqb1 = cA.y;
+    rc.fzc0 = cA.z;
+    rc.fzc1 = cA.w;
+    rc.w = (float)n * (0.5f * g.dv);
+    rc.cz = g.cz;
+    rc.Nb = (float)Nb;
+    rc.Nz = (float)g.nz;
+    rc.qb0 = cF.qb0;
+    rc.qb1 = cF.qb1;
+    rc.qz0 = (long long)n * cF.h0 + g.cz_fx;
+    rc.qz1 = (long long)n * cF.h1;
+    rc.hi_b = (long long)Nb << FX_BITS;
+    rc.hi_z = (long long)g.nz << FX_BITS;
+}
+
+template <typename TX, typename TB, typename TO, int MODE>
+__device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, int s, int iu, int iv,
+                                         float w, float sum, float &r2) {
+    const DevGeom &g = a.g;
+    const float W = cB.x * sqrtf(fmaf(w, w, cB.y));
+    const float ax = W * sum;
+    if (MODE == PROJ_STORE) {
+        ((TO *)a.out)[((size_t)s * g.nv + iv) * g.nu + iu] = from_f32<TO>(ax);
+    } else {
+        const int bv = a.b_views ? a.b_views[s] : s;
+        const float bval = ldg_f32((const TB *)a.b + ((size_t)bv * g.nv + iv) * g.nu + iu);
+        const float r = ax - bval;
+        if (MODE == PROJ_RESID)
+            ((float *)a.out)[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = W * r;
+        r2 += r * r;
+    }
+}
+
 template <typename TX, typename TB, typename TO, int MODE>
 __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
     const DevGeom &g = a.g;
@@ -107,75 +181,42 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
         const float4 cB = g.colB[col];
         const FxCol cF = g.colF[col];
         const bool famY = cB.z != 0.f;
-        const ZLayout &L = a.L;
         const int Na = famY ? g.ny : g.nx;  // planes along the dominant axis
         const int Nb = famY ? g.nx : g.ny;  // in-plane extent
-        const TX *vol = (const TX *)a.vol;
-        const int n = 2 * iv - (g.nv - 1);  // w = n * dv / 2
         RayConst rc;
-        rc.fqb0 = cA.x;
-        rc.fqb1 = cA.y;
-        rc.fzc0 = cA.z;
-        rc.fzc1 = cA.w;
-        rc.w = (float)n * (0.5f * g.dv);
-        rc.cz = g.cz;
-        rc.Nb = (float)Nb;
-        rc.Nz = (float)g.nz;
-        rc.qb0 = cF.qb0;
-        rc.qb1 = cF.qb1;
-        rc.qz0 = (long long)n * cF.h0 + g.cz_fx;
-        rc.qz1 = (long long)n * cF.h1;
-        rc.hi_b = (long long)Nb << FX_BITS;
-        rc.hi_z = (long long)g.nz << FX_BITS;
+        make_ray<TX>(g, cA, cF, Nb, iv, rc);
         int m0 = 1, m1 = 0;
         if (iv < g.nv) plane_range(rc, Na, m0, m1);
+        constexpr int BIG = 1 << 30;
         const bool has = m0 <= m1;
-        const int own0 = has ? m0 : (1 << 30);
-        const int own1 = has ? m1 : -1;
-        const int mu0 = __reduce_min_sync(0xffffffffu, own0);
-        const int mu1 = __reduce_max_sync(0xffffffffu, own1);
-        float acc0 = 0.f, acc1 = 0.f;
-        if (mu0 <= mu1) {
-            const int ps = L.plane_stride(famY);  // next plane
+        // a ray with no sample is pinned to the zero row k = -1 with weight 0
+        if (!has) {
+            rc.qz0 = -(1LL << FX_BITS);
+            rc.qz1 = 0;
+        }
+        // warp union of the intervals, and their common part (rays without samples excluded)
+        const int u0 = __reduce_min_sync(0xffffffffu, has ? m0 : BIG);
+        const int u1 = __reduce_max_sync(0xffffffffu, has ? m1 : -1);
+        const int c0 = __reduce_max_sync(0xffffffffu, has ? m0 : -BIG);
+        const int c1 = __reduce_min_sync(0xffffffffu, has ? m1 : BIG);
+        float acc = 0.f;
+        if (u0 <= u1) {
+            const TX *vol = (const TX *)a.vol;
+            const ZLayout &L = a.L;
+            const int ps = L.plane_stride(famY);    // next plane
             const int bs = L.inplane_stride(famY);  // next in-plane voxel
             // element (b, m, k) = vol + [PL + (m+1)*ps + (b+1)*bs + k]
-            int off_m = L.PL + (mu0 + 1) * ps + bs;
-            long long qb = rc.qb0 + (long long)mu0 * rc.qb1;
-            long long qz = rc.qz0 + (long long)mu0 * rc.qz1;
-#pragma unroll 2
-            for (int m = mu0; m <= mu1; ++m) {
-                const bool in = (m >= own0) & (m <= own1);
-                const int b0 = fx_floor(qb);
-                const float fb = fx_frac(qb);
-                const int k0 = in ? fx_floor(qz) : -1;
-                const float fz = in ? fx_frac(qz) : 0.f;
-                const TX *p = vol + (off_m + b0 * bs + k0);
-                const float v00 = ldg_f32(p), v10 = ldg_f32(p + 1);
-                const float v01 = ldg_f32(p + bs), v11 = ldg_f32(p + bs + 1);
-                const float lo = fmaf(fb, v01 - v00, v00);
-                const float hi = fmaf(fb, v11 - v10, v10);
-                const float val = fmaf(fz, hi - lo, lo);
-                if (m & 1) acc1 += val; else acc0 += val;
-                qb += rc.qb1;
-                qz += rc.qz1;
-                off_m += ps;
-            }
-        }
-        if (iv < g.nv) {
-            const float sum = acc0 + acc1;
-            const float W = cB.x * sqrtf(fmaf(rc.w, rc.w, cB.y));
-            const float ax = W * sum;
-            if (MODE == PROJ_STORE) {
-                ((TO *)a.out)[((size_t)s * g.nv + iv) * g.nu + iu] = from_f32<TO>(ax);
+            const int base = L.PL + ps + bs;
+            const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
+            if (c0 <= c1) {
+                if (u0 < c0) acc += plane_loop<true, TX>(vol, u0, c0 - 1, ps, bs, base, rc, o0, o1);
+                acc += plane_loop<false, TX>(vol, c0, c1, ps, bs, base, rc, o0, o1);
+                if (c1 < u1) acc += plane_loop<true, TX>(vol, c1 + 1, u1, ps, bs, base, rc, o0, o1);
             } else {
-                const int bv = a.b_views ? a.b_views[s] : s;
-                const float bval = ldg_f32((const TB *)a.b + ((size_t)bv * g.nv + iv) * g.nu + iu);
-                const float r = ax - bval;
-                if (MODE == PROJ_RESID)
-                    ((float *)a.out)[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = W * r;
-                r2 = r * r;
+                acc = plane_loop<true, TX>(vol, u0, u1, ps, bs, base, rc, o0, o1);
             }
         }
+        if (iv < g.nv) epilogue<TX, TB, TO, MODE>(a, cB, s, iu, iv, rc.w, acc, r2);
     }
     if (MODE != PROJ_STORE) {
         float vv[1] = {r2};
@@ -219,7 +260,7 @@ __global__ void __launch_bounds__(256) k_weight(const DevGeom g, const TY *__res
 
 template <typename TX, typename TB, typename TO, int MODE>
 cudaError_t launch_t(const ProjArgs &a, int n_sel, cudaStream_t st) {
-    dim3 block(K1_ROWS, K1_COLS);
+    dim3 block(32, K1_COLS);
     dim3 grid((a.g.nu + K1_COLS - 1) / K1_COLS, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
     k1_project<TX, TB, TO, MODE><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
