@@ -214,6 +214,7 @@ def run_ours(args, rank, world, local_rank):
     wl = synth.WORKLOADS[args.workload]
     g = wl.geom
     G, xt, b = make_data(fbl, wl, device)
+    tune = fbl.geometry_autotune(G, fbl.F32, wl.N0)
     params = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
                                 max_backtracks=60)
     S = fbl.fblisa_create(G, params)
@@ -291,7 +292,8 @@ def run_ours(args, rank, world, local_rank):
                            "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                            "frac": (k3_gbs / peaks["hbm_gbs"]) if k3_gbs else None,
                            "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},
-           "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk}
+           "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk,
+           "autotune": tune}
 
     # end to end through the same C-ABI call with host (pinned) buffers
     if args.e2e_steps > 0:

@@ -102,6 +102,7 @@ typedef struct {
     int32_t b_dtype;          /* fbl_dtype of the caller's b */
     int32_t use_graph;        /* 1: run each iteration's line search as one CUDA graph */
     int32_t force_reject;     /* test hook: every trial fails (2.3) */
+    int32_t autotune;         /* 1: time the kernels' launch configurations at creation */
 } fbl_params;
 
 /* Record of one iteration of Algorithm 1. */
@@ -136,6 +137,28 @@ FBL_API void fbl_params_default(fbl_params *p);
  */
 FBL_API fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometry **out);
 FBL_API void geometry_destroy(fbl_geometry *g);
+
+/* Launch configurations tried by the autotuner and their measured times. */
+typedef struct {
+    float k1_ms[4];     /* projector, (cols, split) = (8,1), (8,0), (4,1), (4,0) */
+    float k2_ms[2];     /* backprojector, voxels per lane = 4, 2 */
+    int32_t k1_cols, k1_split, k2_vpl;  /* the chosen configuration */
+} fbl_tune_report;
+
+/*
+ * geometry_autotune -- time the projector and backprojector launch
+ * configurations on this geometry (n_sel views spread over the orbit, storage
+ * x_dtype) and keep the fastest for later calls on g.  Results do not depend
+ * on the configuration beyond FP32 summation order.  Not safe to call while
+ * other calls use g.  report may be NULL.
+ */
+FBL_API fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n_sel, void *stream,
+                                     fbl_tune_report *report);
+
+/* Set the launch configuration by hand: k1_cols in {4, 8}, k1_split in {0, 1},
+ * k2_vpl in {2, 4}; FBL_E_INVAL otherwise. */
+FBL_API fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
+                                       int32_t k2_vpl);
 
 /*
  * project -- y = A_N x (eq. (2.5)'s restricted operator) for the n_sel views

@@ -44,7 +44,7 @@ class fbl_params(ctypes.Structure):
                 ("max_backtracks", ctypes.c_int32), ("proposal", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("x_dtype", ctypes.c_int32),
                 ("b_dtype", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("force_reject", ctypes.c_int32)]
+                ("force_reject", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class fbl_step_stats(ctypes.Structure):
@@ -59,6 +59,12 @@ class fbl_step_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class fbl_tune_report(ctypes.Structure):
+    _fields_ = [("k1_ms", ctypes.c_float * 4), ("k2_ms", ctypes.c_float * 2),
+                ("k1_cols", ctypes.c_int32), ("k1_split", ctypes.c_int32),
+                ("k2_vpl", ctypes.c_int32)]
+
+
 class fbl_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
@@ -69,7 +75,8 @@ PROFILE_CLASSES = ("residual_projection", "objective_projection", "gradient_back
 EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_destroy", "project", "backproject",
            "residual_norm", "prox_reduce", "fblisa_create", "fblisa_destroy", "fblisa_step",
            "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
-           "fbl_epoch_batches", "prox_reduce_static"]
+           "fbl_epoch_batches", "prox_reduce_static", "geometry_autotune",
+           "geometry_set_launch"]
 
 
 def _load():
@@ -83,6 +90,8 @@ def _load():
         "fbl_params_default": (None, [P(fbl_params)]),
         "geometry_create": (st, [P(fbl_geometry_desc), P(vp)]),
         "geometry_destroy": (None, [vp]),
+        "geometry_autotune": (st, [vp, i32, i32, vp, P(fbl_tune_report)]),
+        "geometry_set_launch": (st, [vp, i32, i32, i32]),
         "project": (st, [vp, vp, i32, P(i32), i32, vp, i32, vp]),
         "backproject": (st, [vp, vp, i32, P(i32), i32, vp, i32, vp]),
         "residual_norm": (st, [vp, vp, i32, P(i32), i32, vp, i32, P(dbl), vp]),
@@ -215,6 +224,17 @@ class Geometry:
 
 def geometry_create(desc) -> Geometry:
     return Geometry(desc)
+
+
+def geometry_set_launch(geom: Geometry, k1_cols: int, k1_split: int, k2_vpl: int) -> None:
+    _check(lib.geometry_set_launch(geom.handle, k1_cols, k1_split, k2_vpl))
+
+
+def geometry_autotune(geom: Geometry, x_dtype: int = F32, n_sel: int = 8, stream=None) -> dict:
+    rep = fbl_tune_report()
+    _check(lib.geometry_autotune(geom.handle, x_dtype, n_sel, stream, ctypes.byref(rep)))
+    return {"k1_ms": list(rep.k1_ms), "k2_ms": list(rep.k2_ms), "k1_cols": rep.k1_cols,
+            "k1_split": rep.k1_split, "k2_vpl": rep.k2_vpl}
 
 
 def project(geom: Geometry, x, views: Sequence[int], y=None, y_dtype: Optional[int] = None,

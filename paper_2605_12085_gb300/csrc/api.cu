@@ -273,6 +273,9 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     dg.inv_du = (float)(1.0 / d.du);
     dg.hwu = (float)hw;
     dg.cz_fx = (long long)std::llround(cxyz[2] * FX_ONE);
+    dg.k1_cols = 8;
+    dg.k1_split = 1;
+    dg.k2_vpl = 4;
     // detector rows with a crossing in (k - 1, k + 1) on one column: at most
     // floor(2 max_inv) + 1
     dg.ntap = (int)std::floor(2.0 * max_inv * 1.0001 + 0.002) + 1;
@@ -631,6 +634,7 @@ extern "C" fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g
 // ---------------------------------------------------------------------------
 struct fbl_solver {
     const fbl_geometry *g = nullptr;
+    DevGeom dg;                   // the geometry's tables with this solver's launch configuration
     fbl_params p;
     int device = -1;
     int32_t n_max = 0;
@@ -815,14 +819,14 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     // Step 2b: residual, f_N(x), grad f_N(x)
     int np = 0;
     CK(prof_launch(s, 0, st, [&] {
-           return launch_project(PROJ_RESID, g->dg, s->st, s->L, xdt, s->d_views, N,
+           return launch_project(PROJ_RESID, s->dg, s->st, s->L, xdt, s->d_views, N,
                                  bd, s->p.b_dtype, bmap, s->rt, FBL_F32, s->partials, &np, st);
        }),
        "residual kernel");
     CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
        "reduce");
     CK(prof_launch(s, 2, st, [&] {
-           return launch_backproject(g->dg, s->rt, s->d_views, N, (float)scale, s->grad, st);
+           return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st);
        }),
        "gradient kernel");
     // Step 2c: backtracking on (2.3)
@@ -843,7 +847,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
            "reduce");
         CK(prof_launch(s, 1, st, [&] {
-               return launch_project(PROJ_NORM, g->dg, s->tr, s->L, xdt, s->d_views, N,
+               return launch_project(PROJ_NORM, s->dg, s->tr, s->L, xdt, s->d_views, N,
                                      bd, s->p.b_dtype, bmap, nullptr, FBL_F32, s->partials, &np, st);
            }),
            "objective kernel");
@@ -934,6 +938,141 @@ fbl_status solver_store_x(fbl_solver *s, void *x, bool x_dev, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+
+// Time every launch configuration of the projector (trial-objective mode) and
+// the backprojector on this geometry, with n_sel views spread over the orbit,
+// and keep the fastest in dg.  Buffer contents do not change the work done.
+fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int n_sel,
+                            cudaStream_t st, fbl_tune_report *rep) {
+    const fbl_geometry_desc &d = g->desc;
+    if (n_sel < 1) n_sel = 1;
+    if (n_sel > d.n_views) n_sel = d.n_views;
+    std::vector<int32_t> views(n_sel);
+    for (int q = 0; q < n_sel; ++q) views[q] = (int32_t)((int64_t)q * d.n_views / n_sel);
+    const ZLayout L = layout_for(g, x_dtype);
+    const size_t vbytes = (size_t)L.elems() * dtype_size(x_dtype);
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    const size_t bel = (size_t)n_sel * d.nv * d.nu;
+    const size_t rtel = (size_t)n_sel * d.nu * rt_pitch(d.nv);
+    AsyncBuf vol, b, rt, gz, part, dviews;
+    CK(vol.alloc(vbytes, st), "autotune");
+    CK(cudaMemsetAsync(vol.p, 0x3c, vbytes, st), "autotune");
+    CK(b.alloc(bel * sizeof(float), st), "autotune");
+    CK(cudaMemsetAsync(b.p, 0, bel * sizeof(float), st), "autotune");
+    CK(rt.alloc(rtel * sizeof(float), st), "autotune");
+    CK(cudaMemsetAsync(rt.p, 0x3c, rtel * sizeof(float), st), "autotune");
+    CK(gz.alloc(nvox * sizeof(float), st), "autotune");
+    CK(dviews.alloc((size_t)n_sel * sizeof(int32_t), st), "autotune");
+    CK(cudaMemcpyAsync(dviews.p, views.data(), (size_t)n_sel * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+       "autotune");
+    size_t np = 0;
+    for (int cols : {4, 8}) {
+        DevGeom t = dg;
+        t.k1_cols = cols;
+        np = std::max(np, (size_t)project_num_partials(t, n_sel));
+    }
+    CK(part.alloc(np * sizeof(double), st), "autotune");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "autotune");
+    CK(cudaEventCreate(&e1), "autotune");
+    auto time_it = [&](auto &&launch, float &ms) -> cudaError_t {
+        cudaError_t e = launch();  // warm-up
+        if (e != cudaSuccess) return e;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2; ++r) launch();
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return e;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.5f;
+        return cudaGetLastError();
+    };
+    float best = 1e30f;
+    int qi = 0;
+    for (int cols : {8, 4})
+        for (int split : {1, 0}) {
+            DevGeom t = dg;
+            t.k1_cols = cols;
+            t.k1_split = split;
+            float ms = 0.f;
+            cudaError_t e = time_it(
+                [&] {
+                    return launch_project(PROJ_NORM, t, vol.p, L, x_dtype, (const int32_t *)dviews.p, n_sel,
+                                          b.p, FBL_F32, nullptr, nullptr, FBL_F32, (double *)part.p, nullptr,
+                                          st);
+                },
+                ms);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "autotune projector");
+            }
+            if (rep && qi < 4) rep->k1_ms[qi] = ms;
+            ++qi;
+            if (ms < best) {
+                best = ms;
+                dg.k1_cols = cols;
+                dg.k1_split = split;
+            }
+        }
+    best = 1e30f;
+    qi = 0;
+    for (int vpl : {4, 2}) {
+        DevGeom t = dg;
+        t.k2_vpl = vpl;
+        float ms = 0.f;
+        cudaError_t e = time_it(
+            [&] {
+                return launch_backproject(t, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f,
+                                          (float *)gz.p, st);
+            },
+            ms);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune backprojector");
+        }
+        if (rep && qi < 2) rep->k2_ms[qi] = ms;
+        ++qi;
+        if (ms < best) {
+            best = ms;
+            dg.k2_vpl = vpl;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rep) {
+        rep->k1_cols = dg.k1_cols;
+        rep->k1_split = dg.k1_split;
+        rep->k2_vpl = dg.k2_vpl;
+    }
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n_sel, void *stream,
+                                        fbl_tune_report *report) {
+    if (!g) return fail(FBL_E_INVAL, "geometry_autotune: null geometry");
+    if (!valid_dtype(x_dtype)) return fail(FBL_E_INVAL, "geometry_autotune: bad dtype");
+    fbl_status st = check_device(g->device);
+    if (st) return st;
+    if (report) std::memset(report, 0, sizeof *report);
+    return autotune_devgeom(g, g->dg, x_dtype, n_sel, (cudaStream_t)stream, report);
+}
+
+extern "C" fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
+                                          int32_t k2_vpl) {
+    if (!g) return fail(FBL_E_INVAL, "geometry_set_launch: null geometry");
+    if ((k1_cols != 4 && k1_cols != 8) || (k1_split != 0 && k1_split != 1) || (k2_vpl != 2 && k2_vpl != 4))
+        return fail(FBL_E_INVAL, "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1}, k2_vpl in {2,4}");
+    g->dg.k1_cols = k1_cols;
+    g->dg.k1_split = k1_split;
+    g->dg.k2_vpl = k2_vpl;
+    return FBL_OK;
+}
+
 extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, fbl_solver **out) {
     if (!g || !p || !out) return fail(FBL_E_INVAL, "fblisa_create: null argument");
     *out = nullptr;
@@ -951,6 +1090,7 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     if (p->use_graph != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: graph mode not available");
     auto s = new fbl_solver();
     s->g = g;
+    s->dg = g->dg;
     s->p = *p;
     s->device = g->device;
     s->n_max = n_max;
@@ -974,6 +1114,17 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
         solver_free(s);
         delete s;
         return cuda_fail(e, "fblisa_create");
+    }
+    if (p->autotune) {
+        const int32_t Nt = std::min(n_max, std::max(p->N0, 1));
+        fbl_status ts = autotune_devgeom(g, s->dg, p->x_dtype, Nt, nullptr, nullptr);
+        if (ts) {
+            std::string keep = g_last_error;
+            solver_free(s);
+            delete s;
+            g_last_error = keep;
+            return ts;
+        }
     }
     *out = s;
     return FBL_OK;

@@ -116,6 +116,10 @@ struct DevGeom {
     float sod, sdd, inv_du;
     float hwu;                   // half width, in columns, of a voxel's column footprint
     int ntap;                    // detector rows that can touch one voxel in one column
+    // launch configuration (chosen by the autotuner; defaults 8 / 1 / 4)
+    int k1_cols;                 // projector: detector columns per block (4 or 8)
+    int k1_split;                // projector: unmasked middle phase of the plane loop (0 or 1)
+    int k2_vpl;                  // backprojector: consecutive voxels per lane (2 or 4)
     long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
     const FxCol *colF;           // [n_views][nu] exact fixed-point constants

@@ -7,8 +7,9 @@
 // y-planes), with weight wb * wz: wb from the in-plane crossing q_b(m) of its
 // detector column, wz from the vertical crossing q_z(m) of its row.
 //
-// Work decomposition.  A warp owns 128 voxels of one (i, j) column along z
-// (lane l holds the four consecutive voxels k0 + 4l .. k0 + 4l + 3).  Everything that depends only on
+// Work decomposition.  A warp owns 32*VPL voxels of one (i, j) column along z
+// (lane l holds the VPL consecutive voxels k0 + VPL*l ...; VPL = 2 or 4,
+// chosen by the autotuner).  Everything that depends only on
 // (i, j) and the view -- the candidate columns within hwu of the voxel
 // column's projection, each column's family, plane m, exact in-plane weight
 // wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
@@ -28,8 +29,6 @@ namespace {
 
 constexpr int K2_LANES = 32;
 constexpr int K2_WARPS = 8;   // consecutive i per block
-constexpr int K2_VPL = 4;     // voxels per lane
-constexpr int K2_KSPAN = K2_LANES * K2_VPL;
 
 struct BpArgs {
     DevGeom g;
@@ -40,8 +39,9 @@ struct BpArgs {
     float *gzi;
 };
 
-template <int NTAP>
+template <int NTAP, int K2_VPL>
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
+    constexpr int K2_KSPAN = K2_LANES * K2_VPL;
     const DevGeom &g = a.g;
     const int lane = threadIdx.x;
     const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
@@ -134,17 +134,27 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
     a.scale = scale;
     a.gzi = gzi;
     dim3 block(K2_LANES, K2_WARPS);
-    dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_KSPAN - 1) / K2_KSPAN);
+    const int vpl = g.k2_vpl == 2 ? 2 : 4;
+    dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
+#define FBL_K2_CASE(NT)                                                  \
+    case NT:                                                             \
+        if (vpl == 2) k2_backproject<NT, 2><<<grid, block, 0, st>>>(a); \
+        else k2_backproject<NT, 4><<<grid, block, 0, st>>>(a);          \
+        break;
     switch (g.ntap) {  // rows per voxel and column, fixed per geometry (<= RT_PAD)
-        case 1: k2_backproject<1><<<grid, block, 0, st>>>(a); break;
-        case 2: k2_backproject<2><<<grid, block, 0, st>>>(a); break;
-        case 3: k2_backproject<3><<<grid, block, 0, st>>>(a); break;
-        case 4: k2_backproject<4><<<grid, block, 0, st>>>(a); break;
-        case 5: k2_backproject<5><<<grid, block, 0, st>>>(a); break;
-        case 6: k2_backproject<6><<<grid, block, 0, st>>>(a); break;
-        case 7: k2_backproject<7><<<grid, block, 0, st>>>(a); break;
-        default: k2_backproject<8><<<grid, block, 0, st>>>(a); break;
+        FBL_K2_CASE(1)
+        FBL_K2_CASE(2)
+        FBL_K2_CASE(3)
+        FBL_K2_CASE(4)
+        FBL_K2_CASE(5)
+        FBL_K2_CASE(6)
+        FBL_K2_CASE(7)
+        default:
+            if (vpl == 2) k2_backproject<8, 2><<<grid, block, 0, st>>>(a);
+            else k2_backproject<8, 4><<<grid, block, 0, st>>>(a);
+            break;
     }
+#undef FBL_K2_CASE
     return cudaGetLastError();
 }
 

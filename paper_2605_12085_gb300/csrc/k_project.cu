@@ -31,8 +31,6 @@ namespace fbl {
 namespace {
 
 constexpr int K1_ROWS = 32;  // detector rows per warp: one ray per lane
-constexpr int K1_COLS = 8;   // warps: consecutive detector columns
-constexpr int K1_NT = 32 * K1_COLS;
 
 struct ProjArgs {
     DevGeom g;
@@ -166,11 +164,11 @@ __device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, in
     }
 }
 
-template <typename TX, typename TB, typename TO, int MODE>
-__global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
+template <typename TX, typename TB, typename TO, int MODE, int COLS, bool SPLIT>
+__global__ void __launch_bounds__(32 * COLS) k1_project(const ProjArgs a) {
     const DevGeom &g = a.g;
     const int lane = threadIdx.x;
-    const int iu = blockIdx.x * K1_COLS + threadIdx.y;  // uniform over the warp
+    const int iu = blockIdx.x * COLS + threadIdx.y;  // uniform over the warp
     const int s = blockIdx.y;
     const int iv = blockIdx.z * K1_ROWS + lane;
     float r2 = 0.f;
@@ -208,7 +206,7 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
             // element (b, m, k) = vol + [PL + (m+1)*ps + (b+1)*bs + k]
             const int base = L.PL + ps + bs;
             const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
-            if (c0 <= c1) {
+            if (SPLIT && c0 <= c1) {
                 if (u0 < c0) acc += plane_loop<true, TX>(vol, u0, c0 - 1, ps, bs, base, rc, o0, o1);
                 acc += plane_loop<false, TX>(vol, c0, c1, ps, bs, base, rc, o0, o1);
                 if (c1 < u1) acc += plane_loop<true, TX>(vol, c1 + 1, u1, ps, bs, base, rc, o0, o1);
@@ -221,7 +219,7 @@ __global__ void __launch_bounds__(K1_NT) k1_project(const ProjArgs a) {
     if (MODE != PROJ_STORE) {
         float vv[1] = {r2};
         double out[1];
-        block_sum_f64<K1_NT, 1>(vv, out);
+        block_sum_f64<32 * COLS, 1>(vv, out);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             a.partials[blk] = out[0];
@@ -260,9 +258,16 @@ __global__ void __launch_bounds__(256) k_weight(const DevGeom g, const TY *__res
 
 template <typename TX, typename TB, typename TO, int MODE>
 cudaError_t launch_t(const ProjArgs &a, int n_sel, cudaStream_t st) {
-    dim3 block(32, K1_COLS);
-    dim3 grid((a.g.nu + K1_COLS - 1) / K1_COLS, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
-    k1_project<TX, TB, TO, MODE><<<grid, block, 0, st>>>(a);
+    const int cols = a.g.k1_cols == 4 ? 4 : 8;
+    dim3 block(32, cols);
+    dim3 grid((a.g.nu + cols - 1) / cols, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
+    if (cols == 4) {
+        if (a.g.k1_split) k1_project<TX, TB, TO, MODE, 4, true><<<grid, block, 0, st>>>(a);
+        else k1_project<TX, TB, TO, MODE, 4, false><<<grid, block, 0, st>>>(a);
+    } else {
+        if (a.g.k1_split) k1_project<TX, TB, TO, MODE, 8, true><<<grid, block, 0, st>>>(a);
+        else k1_project<TX, TB, TO, MODE, 8, false><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -291,7 +296,8 @@ cudaError_t launch_bdt(int mode, int b_dtype, int out_dtype, const ProjArgs &a, 
 }  // namespace
 
 int project_num_partials(const DevGeom &g, int n_sel) {
-    return ((g.nu + K1_COLS - 1) / K1_COLS) * n_sel * ((g.nv + K1_ROWS - 1) / K1_ROWS);
+    const int cols = g.k1_cols == 4 ? 4 : 8;
+    return ((g.nu + cols - 1) / cols) * n_sel * ((g.nv + K1_ROWS - 1) / K1_ROWS);
 }
 
 cudaError_t launch_project(int mode, const DevGeom &g, const void *vol, ZLayout L, int x_dtype,
