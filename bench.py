@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default="c3_512")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", type=int, default=1, help="also time BF16/FP16 storage")
+    ap.add_argument("--variant-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -294,6 +296,34 @@ def run_ours(args, rank, world, local_rank):
                            "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},
            "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk,
            "autotune": tune}
+
+    # storage-precision variants (BF16 / FP16 iterates and data, FP32 arithmetic)
+    if args.variants:
+        import torch
+        variants = {}
+        for name, code, td in (("bf16", fbl.BF16, torch.bfloat16), ("f16", fbl.F16, torch.float16)):
+            bv = b.to(td)
+            pv = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0,
+                                    seed=wl.seed_batches, max_backtracks=60, x_dtype=code,
+                                    b_dtype=code, autotune=1)
+            Sv = fbl.fblisa_create(G, pv)
+            xv = torch.zeros(g.vol_shape, dtype=td, device=device)
+            for _ in range(2):
+                Sv.step(xv, bv)
+            torch.cuda.synchronize(device)
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            stv = [Sv.step(xv, bv) for _ in range(args.variant_steps)]
+            v1.record(stream)
+            torch.cuda.synchronize(device)
+            vms = v0.elapsed_time(v1)
+            uv = sum(step_units(st, g) for st in stv)
+            variants[name] = {"value": uv / (vms * 1e-3) / 1e9, "unit": UNIT,
+                              "ms_per_step": vms / len(stv), "steps": len(stv),
+                              "backtracks_per_step": statistics.mean(st["backtracks"] for st in stv)}
+            del Sv, xv, bv
+        out["precision_variants"] = variants
 
     # end to end through the same C-ABI call with host (pinned) buffers
     if args.e2e_steps > 0:
