@@ -301,11 +301,14 @@ def run_ours(args, rank, world, local_rank):
     if args.variants:
         import torch
         variants = {}
-        for name, code, td in (("bf16", fbl.BF16, torch.bfloat16), ("f16", fbl.F16, torch.float16)):
+        for name, code, td, graph in (("f32_graph", fbl.F32, torch.float32, 1),
+                                      ("bf16", fbl.BF16, torch.bfloat16, 0),
+                                      ("f16", fbl.F16, torch.float16, 0),
+                                      ("bf16_graph", fbl.BF16, torch.bfloat16, 1)):
             bv = b.to(td)
             pv = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0,
                                     seed=wl.seed_batches, max_backtracks=60, x_dtype=code,
-                                    b_dtype=code, autotune=1)
+                                    b_dtype=code, autotune=1, use_graph=graph)
             Sv = fbl.fblisa_create(G, pv)
             xv = torch.zeros(g.vol_shape, dtype=td, device=device)
             for _ in range(2):
@@ -323,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
                               "ms_per_step": vms / len(stv), "steps": len(stv),
                               "backtracks_per_step": statistics.mean(st["backtracks"] for st in stv)}
             del Sv, xv, bv
-        out["precision_variants"] = variants
+        out["variants"] = variants
 
     # end to end through the same C-ABI call with host (pinned) buffers
     if args.e2e_steps > 0:

@@ -100,7 +100,8 @@ typedef struct {
     uint64_t seed;            /* mini-batch permutation seed */
     int32_t x_dtype;          /* fbl_dtype of the caller's x and the solver's iterates */
     int32_t b_dtype;          /* fbl_dtype of the caller's b */
-    int32_t use_graph;        /* 1: run each iteration's line search as one CUDA graph */
+    int32_t use_graph;        /* 1: run each iteration, backtracking included, as one CUDA graph
+                                 whose WHILE node repeats the trial until (2.3) holds */
     int32_t force_reject;     /* test hook: every trial fails (2.3) */
     int32_t autotune;         /* 1: time the kernels' launch configurations at creation */
 } fbl_params;
@@ -201,6 +202,19 @@ FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, i
                        double mu, void *xbar, double *out3_host, void *stream);
 
 /*
+ * evaluate -- the full objective of eq. (2.1) over all n_views views and the
+ * relative error used in Sec. 3 ("Similarity measures"):
+ *   out3_host[0] = F(x) = 1/2 ||A x - b||^2 + mu ||x||_1   (x >= 0 assumed),
+ *   out3_host[1] = 1/2 ||A x - b||^2,
+ *   out3_host[2] = RE = ||x - x_true|| / ||x_true||   (0 when x_true is NULL).
+ * x, x_true: [nz][ny][nx] of x_dtype; b: the full sinogram of b_dtype.  FP32
+ * projection, FP64 sums.  Returns after the values are on the host.
+ */
+FBL_API fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtype, const void *b,
+                            int32_t b_dtype, double mu, const void *x_true, double *out3_host,
+                            void *stream);
+
+/*
  * prox_reduce_static -- the same computation and outputs as prox_reduce, for
  * callers that must not allocate device memory: code that runs under a
  * fixed memory budget reserved up front, host applications or plugins whose
@@ -258,8 +272,10 @@ FBL_API fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t epo
  * profiling enabled the solver brackets each of its kernel launches with
  * CUDA events on the launching stream.  Classes: 0 residual projection
  * (Step 2b), 1 trial-objective projection (Step 2c), 2 gradient
- * backprojection, 3 prox + reductions, 4 final FP64 reductions, 5 volume
- * packing.  Launch counts are kept whether or not timing is enabled.
+ * backprojection, 3 prox + reductions, 4 final FP64 reductions and device
+ * line-search control, 5 volume layout conversion.  Launch counts are kept
+ * whether or not timing is enabled; in graph mode (use_graph) kernels run
+ * inside one graph per iteration and only their counts are kept.
  */
 enum { FBL_PROF_CLASSES = 6 };
 typedef struct {

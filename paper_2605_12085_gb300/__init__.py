@@ -76,7 +76,7 @@ EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_
            "residual_norm", "prox_reduce", "fblisa_create", "fblisa_destroy", "fblisa_step",
            "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
            "fbl_epoch_batches", "prox_reduce_static", "geometry_autotune",
-           "geometry_set_launch"]
+           "geometry_set_launch", "evaluate"]
 
 
 def _load():
@@ -97,6 +97,7 @@ def _load():
         "residual_norm": (st, [vp, vp, i32, P(i32), i32, vp, i32, P(dbl), vp]),
         "prox_reduce": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
         "prox_reduce_static": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
+        "evaluate": (st, [vp, vp, i32, vp, i32, dbl, vp, P(dbl), vp]),
         "fblisa_create": (st, [vp, P(fbl_params), P(vp)]),
         "fblisa_destroy": (None, [vp]),
         "fblisa_step": (st, [vp, vp, vp, P(fbl_step_stats), vp]),
@@ -268,6 +269,15 @@ def residual_norm(geom: Geometry, x, views: Sequence[int], b, stream=None) -> fl
                              v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), v.size, _ptr(b),
                              _dtype_code(b), ctypes.byref(rho), _stream(x, b, stream=stream)))
     return rho.value
+
+
+def evaluate(geom: Geometry, x, b, mu: float, x_true=None, stream=None):
+    """(F(x), 1/2||Ax-b||^2, RE) over all views (RE = 0 without x_true)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib.evaluate(geom.handle, _ptr(x), _dtype_code(x), _ptr(b), _dtype_code(b), float(mu),
+                        None if x_true is None else _ptr(x_true), out,
+                        _stream(x, b, stream=stream)))
+    return out[0], out[1], out[2]
 
 
 def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):

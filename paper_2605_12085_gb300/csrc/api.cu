@@ -593,6 +593,66 @@ extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_
     return FBL_OK;
 }
 
+extern "C" fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtype, const void *b,
+                               int32_t b_dtype, double mu, const void *x_true, double *out3_host,
+                               void *stream) {
+    if (!g || !x || !b || !out3_host) return fail(FBL_E_INVAL, "evaluate: null argument");
+    if (!valid_dtype(x_dtype) || !valid_dtype(b_dtype)) return fail(FBL_E_INVAL, "evaluate: bad dtype");
+    fbl_status st = check_device(g->device);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fbl_geometry_desc &d = g->desc;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    const size_t xbytes = nvox * dtype_size(x_dtype);
+    AsyncBuf xs, xts, pv, dviews, bs, part, res;
+    const void *xd = nullptr, *xtd = nullptr;
+    if ((st = device_input(x, xbytes, xs, &xd, s))) return st;
+    if (x_true && (st = device_input(x_true, xbytes, xts, &xtd, s))) return st;
+    ZLayout L;
+    if ((st = pack_volume(g, xd, x_dtype, pv, L, s))) return st;
+    std::vector<int32_t> all(d.n_views);
+    for (int v = 0; v < d.n_views; ++v) all[v] = v;
+    if ((st = upload_views(all.data(), d.n_views, dviews, s))) return st;
+    const bool b_dev = is_device_ptr(b);
+    const int chunk = std::min(d.n_views, 256);
+    const int npmax = std::max(project_num_partials(g->dg, chunk), 3 * prox_flat_num_partials((int64_t)nvox));
+    const int nchunks = (d.n_views + chunk - 1) / chunk;
+    CK(part.alloc((size_t)npmax * sizeof(double), s), "partials");
+    CK(res.alloc((size_t)(nchunks + 3) * sizeof(double), s), "results");
+    const size_t per_view = (size_t)d.nv * d.nu * dtype_size(b_dtype);
+    if (!b_dev) CK(bs.alloc(per_view * chunk, s), "data staging");
+    for (int c = 0; c < nchunks; ++c) {
+        const int v0 = c * chunk, nsel = std::min(chunk, d.n_views - v0);
+        const void *bd = b;
+        const int32_t *bmap = (const int32_t *)dviews.p + v0;
+        if (!b_dev) {
+            CK(cudaMemcpyAsync(bs.p, (const char *)b + per_view * v0, per_view * nsel,
+                               cudaMemcpyHostToDevice, s),
+               "data H2D");
+            bd = bs.p;
+            bmap = nullptr;
+        }
+        int np = 0;
+        CK(launch_project(PROJ_NORM, g->dg, pv.p, L, x_dtype, (const int32_t *)dviews.p + v0, nsel, bd,
+                          b_dtype, bmap, nullptr, FBL_F32, (double *)part.p, &np, s),
+           "objective kernel");
+        CK(launch_reduce((const double *)part.p, np, np, 1, (double *)res.p + c, s), "reduce");
+    }
+    int nn = 0;
+    CK(launch_norms(xd, xtd, x_dtype, (int64_t)nvox, (double *)part.p, &nn, s), "norms kernel");
+    CK(launch_reduce((const double *)part.p, nn, nn, 3, (double *)res.p + nchunks, s), "reduce");
+    std::vector<double> h(nchunks + 3);
+    CK(cudaMemcpyAsync(h.data(), res.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    CK(cudaStreamSynchronize(s), "evaluate");
+    double rho = 0.0;
+    for (int c = 0; c < nchunks; ++c) rho += h[c];
+    out3_host[1] = 0.5 * rho;
+    out3_host[0] = 0.5 * rho + mu * h[nchunks];
+    out3_host[2] = x_true ? (h[nchunks + 2] > 0 ? std::sqrt(h[nchunks + 1] / h[nchunks + 2]) : 0.0) : 0.0;
+    if (!std::isfinite(out3_host[0])) return fail(FBL_E_NONFINITE, "evaluate: non-finite objective");
+    return FBL_OK;
+}
+
 extern "C" fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *gr, int64_t n,
                                   double alpha, double mu, void *xbar, double *out3_host,
                                   void *stream) {
@@ -668,6 +728,18 @@ struct fbl_solver {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_next = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    // graph mode: one executable graph per (batch size, data pointer, buffer parity)
+    struct GraphEntry {
+        int N;
+        const void *bd;
+        const int32_t *bmap;
+        void *st, *tr;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams
+    LSState *d_ls = nullptr;                      // line-search state (device)
+    LSState *h_ls = nullptr;                      // its host copy (pinned)
 };
 
 namespace {
@@ -686,6 +758,12 @@ void solver_free(fbl_solver *s) {
     cudaFreeHost(s->h_sc);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->ev_pool.clear();
+    for (auto &ge : s->graphs) cudaGraphExecDestroy(ge.exec);
+    s->graphs.clear();
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->cap2) cudaStreamDestroy(s->cap2);
+    cudaFree(s->d_ls);
+    cudaFreeHost(s->h_ls);
 }
 
 cudaEvent_t prof_event(fbl_solver *s) {
@@ -722,10 +800,16 @@ void prof_flush(fbl_solver *s) {
     s->ev_next = 0;
 }
 
+void drop_graphs(fbl_solver *s) {
+    for (auto &ge : s->graphs) cudaGraphExecDestroy(ge.exec);
+    s->graphs.clear();
+}
+
 fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
     const fbl_geometry_desc &d = s->g->desc;
     const size_t need = (size_t)N * d.nu * rt_pitch(d.nv);
     if (need > s->rt_cap) {
+        drop_graphs(s);  // captured graphs hold the old addresses
         cudaFree(s->rt);
         s->rt = nullptr;
         s->rt_cap = 0;
@@ -736,6 +820,7 @@ fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
     const size_t np = std::max((size_t)project_num_partials(s->g->dg, N),
                                (size_t)3 * prox_zi_num_partials(d.nx, d.ny, d.nz));
     if (np > s->partials_cap) {
+        drop_graphs(s);
         cudaFree(s->partials);
         s->partials = nullptr;
         s->partials_cap = 0;
@@ -757,6 +842,64 @@ void begin_epoch_if_needed(fbl_solver *s) {
     s->iters_epoch = (d.n_views + s->N_t - 1) / s->N_t;
     s->iter_in_epoch = 0;
     batches(s->p.seed, s->epoch, d.n_views, s->N_t, s->epoch_views);
+}
+
+// Capture one FB-LISA iteration (Steps 2b-2c) as a graph: residual,
+// gradient, line-search init, then a WHILE node whose body is one trial
+// (prox, reductions, trial objective, decision), then the copy of the
+// line-search state to the host.
+fbl_status build_graph(fbl_solver *s, fbl_solver::GraphEntry &ge) {
+    const fbl_geometry_desc &d = s->g->desc;
+    if (!s->cap) CK(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking), "capture stream");
+    if (!s->cap2) CK(cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking), "capture stream");
+    const int xdt = s->p.x_dtype, N = ge.N;
+    const float scale = (float)((double)d.n_views / (double)N);
+    cudaStream_t cs = s->cap, cb = s->cap2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int np = 0, npp = 0, np2 = 0;
+    cudaError_t e = launch_project(PROJ_RESID, s->dg, ge.st, s->L, xdt, s->d_views, N, ge.bd,
+                                   s->p.b_dtype, ge.bmap, s->rt, FBL_F32, s->partials, &np, cs);
+    if (e == cudaSuccess) e = launch_reduce(s->partials, np, np, 1, s->d_sc + 0, cs);
+    if (e == cudaSuccess) e = launch_backproject(s->dg, s->rt, s->d_views, N, scale, s->grad, cs);
+    if (e == cudaSuccess) e = launch_ls_init(s->d_ls, cs);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t eb = launch_prox_zi_dev(ge.st, s->L, s->grad, s->d_ls, ge.tr, xdt, s->partials, &npp, cb);
+            if (eb == cudaSuccess) eb = launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, cb);
+            if (eb == cudaSuccess)
+                eb = launch_project(PROJ_NORM, s->dg, ge.tr, s->L, xdt, s->d_views, N, ge.bd, s->p.b_dtype,
+                                    ge.bmap, nullptr, FBL_F32, s->partials, &np2, cb);
+            if (eb == cudaSuccess) eb = launch_reduce(s->partials, np2, np2, 1, s->d_sc + 4, cb);
+            if (eb == cudaSuccess) eb = launch_ls_decide(s->d_ls, s->d_sc, cond, cb);
+            cudaError_t ee = cudaStreamEndCapture(cb, &body);
+            e = eb != cudaSuccess ? eb : ee;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_ls, s->d_ls, sizeof(LSState), cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture of the iteration");
+    return FBL_OK;
 }
 
 // One iteration of Algorithm 1 on the solver's state (s->st).
@@ -797,6 +940,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     if (!b_dev) {
         const size_t per_view = (size_t)d.nv * d.nu * dtype_size(s->p.b_dtype);
         if (per_view * N > s->bstage_cap) {
+            drop_graphs(s);
             cudaFree(s->bstage);
             s->bstage = nullptr;
             s->bstage_cap = 0;
@@ -816,6 +960,73 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     }
     const int xdt = s->p.x_dtype;
     const double scale = (double)d.n_views / (double)N;
+    if (s->p.use_graph) {
+        // the whole iteration, backtracking included, as one graph launch
+        fbl_solver::GraphEntry *ge = nullptr;
+        for (auto &c : s->graphs)
+            if (c.N == N && c.bd == bd && c.bmap == bmap && c.st == s->st && c.tr == s->tr) ge = &c;
+        if (!ge) {
+            if (s->graphs.size() >= 8) {
+                cudaGraphExecDestroy(s->graphs.front().exec);
+                s->graphs.erase(s->graphs.begin());
+            }
+            fbl_solver::GraphEntry ne{N, bd, bmap, s->st, s->tr, nullptr};
+            fbl_status bs = build_graph(s, ne);
+            if (bs) {
+                restore();
+                return bs;
+            }
+            s->graphs.push_back(ne);
+            ge = &s->graphs.back();
+        }
+        LSState cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.alpha_init = s->p.alpha0;
+        cfg.beta = s->p.beta;
+        cfg.mu = s->p.mu;
+        cfg.scale = scale;
+        cfg.max_backtracks = s->p.max_backtracks;
+        cfg.force_reject = s->p.force_reject;
+        *s->h_ls = cfg;
+        CK(cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(LSState), cudaMemcpyHostToDevice, st), "line-search state");
+        CK(cudaGraphLaunch(ge->exec, st), "graph launch");
+        CK(cudaStreamSynchronize(st), "graph iteration");
+        const LSState r = *s->h_ls;
+        const int trials = r.trials + 1;
+        s->prof_launches[0] += 1;
+        s->prof_launches[2] += 1;
+        s->prof_launches[1] += trials;
+        s->prof_launches[3] += trials;
+        s->prof_launches[4] += 2 + 3 * trials;
+        const bool accepted = r.status == FBL_OK && r.accepted;
+        if (stats) {
+            stats->k = s->k;
+            stats->epoch = s->epoch;
+            stats->N_t = N;
+            stats->backtracks = r.trials;
+            stats->alpha = r.alpha;
+            stats->alpha_init = s->p.alpha0;
+            stats->rho0 = r.rho0;
+            stats->f_x = r.f_x;
+            stats->f_xbar = r.f_xbar;
+            stats->gTd = r.gTd;
+            stats->dnorm2 = r.dd;
+            stats->margin = r.rhs - r.f_xbar;
+            stats->status = accepted ? FBL_OK : r.status;
+        }
+        if (!accepted) {
+            restore();
+            if (r.status == FBL_E_NONFINITE)
+                return fail(FBL_E_NONFINITE, "fblisa_step: non-finite objective or reduction at k=%lld",
+                            (long long)s->k);
+            return fail(FBL_E_LINESEARCH, "fblisa_step: no step passed (2.3) within %d backtracks",
+                        s->p.max_backtracks);
+        }
+        std::swap(s->st, s->tr);
+        s->k += 1;
+        s->iter_in_epoch += 1;
+        return FBL_OK;
+    }
     // Step 2b: residual, f_N(x), grad f_N(x)
     int np = 0;
     CK(prof_launch(s, 0, st, [&] {
@@ -1087,7 +1298,6 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     if (p->N0 < 1 || p->N0 > n_max || n_max > d.n_views)
         return fail(FBL_E_INVAL, "fblisa_create: need 1 <= N0 <= n_max <= n_views");
     if (p->proposal != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: learned proposal not available");
-    if (p->use_graph != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: graph mode not available");
     auto s = new fbl_solver();
     s->g = g;
     s->dg = g->dg;
@@ -1110,6 +1320,8 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_views, (size_t)d.n_views * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_sc, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ls, sizeof(LSState));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_ls, sizeof(LSState));
     if (e != cudaSuccess) {
         solver_free(s);
         delete s;

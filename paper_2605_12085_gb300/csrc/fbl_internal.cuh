@@ -180,6 +180,27 @@ cudaError_t launch_prox_flat_grid(const void *x, const float *gr, int64_t n, flo
                                   void *xbar, int dtype, int nb, double *partials,
                                   cudaStream_t st);
 
+// partials[3][nb]: sum |x|, sum (x - xr)^2, sum xr^2 (xr may be NULL).
+cudaError_t launch_norms(const void *x, const void *xr, int dtype, int64_t n, double *partials,
+                         int *n_partials, cudaStream_t st);
+
+// Line-search state of one graph-captured iteration (device memory).
+struct LSState {
+    double alpha_init, alpha, beta, mu, scale;  // scale = n_theta / N_t
+    double rho0, gTd, dd, rho1, f_x, f_xbar, rhs;
+    int trials, max_backtracks, accepted, status, force_reject, pad;
+};
+
+cudaError_t launch_ls_init(LSState *ls, cudaStream_t st);
+// Evaluate (2.3) on sc = [rho0, gTd, dd, l1, rho1]; accept, or shrink the step
+// and request another trial (the WHILE condition), or stop with a status.
+cudaError_t launch_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond,
+                             cudaStream_t st);
+// launch_prox_zi with alpha and mu read from the line-search state.
+cudaError_t launch_prox_zi_dev(const void *vol, ZLayout L, const float *gzi, const LSState *ls,
+                               void *trial, int dtype, double *partials, int *n_partials,
+                               cudaStream_t st);
+
 // Record the message returned by fbl_last_error() on this thread.
 void set_last_error(const char *msg);
 

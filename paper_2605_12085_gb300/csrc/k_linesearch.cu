@@ -1,0 +1,131 @@
+// Device-side control of the backtracking line search (Algorithm 1, Step 2c)
+// for the graph-captured iteration: the prox kernel reads the trial step from
+// device memory, and after each trial a one-thread kernel evaluates the
+// sufficient-decrease test (2.3) in FP64 and sets the condition of the
+// graph's WHILE node.  The arithmetic is the host loop's, operation by
+// operation, with explicitly rounded FP64 intrinsics (no contraction into
+// FMA), so both modes take identical decisions.
+#include <math.h>
+
+#include "fbl_internal.cuh"
+#include "fbl_reduce.cuh"
+
+namespace fbl {
+namespace {
+
+__global__ void k_ls_init(LSState *ls) {
+    ls->alpha = ls->alpha_init;
+    ls->trials = 0;
+    ls->accepted = 0;
+    ls->status = FBL_OK;
+}
+
+// sc: [rho0, gTd, dd, l1, rho1] as reduced by the preceding kernels.
+__global__ void k_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond) {
+    const double rho0 = sc[0], gTd = sc[1], dd = sc[2], rho1 = sc[4];
+    const double alpha = ls->alpha;
+    const double half_scale = __dmul_rn(0.5, ls->scale);
+    const double f_x = __dmul_rn(half_scale, rho0);
+    const double f_xb = __dmul_rn(half_scale, rho1);
+    const double rhs = __dadd_rn(__dadd_rn(f_x, gTd), __ddiv_rn(dd, __dmul_rn(2.0, alpha)));
+    ls->rho0 = rho0;
+    ls->gTd = gTd;
+    ls->dd = dd;
+    ls->rho1 = rho1;
+    ls->f_x = f_x;
+    ls->f_xbar = f_xb;
+    ls->rhs = rhs;
+    unsigned int more = 0;
+    if (!isfinite(f_x) || !isfinite(f_xb) || !isfinite(rhs)) {
+        ls->status = FBL_E_NONFINITE;
+    } else if (!ls->force_reject && f_xb <= rhs) {
+        ls->accepted = 1;
+    } else if (ls->trials >= ls->max_backtracks) {
+        ls->status = FBL_E_LINESEARCH;
+    } else {
+        ls->trials += 1;
+        ls->alpha = __dmul_rn(alpha, ls->beta);
+        more = 1;
+    }
+    cudaGraphSetConditional(cond, more);
+}
+
+// Prox + reductions with the step taken from the line-search state.
+constexpr int PZ_TX = 64;
+constexpr int PZ_TY = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi_dev(const T *__restrict__ vol, ZLayout L,
+                                                              const float *__restrict__ gzi,
+                                                              const LSState *ls, T *__restrict__ trial,
+                                                              double *__restrict__ partials) {
+    const double a = ls->alpha;
+    const float alpha = (float)a, amu = (float)(a * ls->mu);
+    const int row = blockIdx.x * PZ_TY + threadIdx.y;
+    float sums[3] = {0.f, 0.f, 0.f};
+    if (row < L.nx * L.ny) {
+        const int j = row / L.nx, i = row - j * L.nx;
+        const int64_t base = L.index(i, j, 0);
+        const T *src = vol + base;
+        T *dst = trial + base;
+        const float *gr = gzi + (size_t)row * L.nz;
+        for (int k = threadIdx.x; k < L.nz; k += PZ_TX) {
+            const float x = to_f32(src[k]);
+            const float gg = gr[k];
+            const float xb = fmaxf(fmaf(-alpha, gg, x) - amu, 0.f);
+            const T xs = from_f32<T>(xb);
+            const float xr = to_f32(xs);
+            dst[k] = xs;
+            const float d = xr - x;
+            sums[0] = fmaf(gg, d, sums[0]);
+            sums[1] = fmaf(d, d, sums[1]);
+            sums[2] += xr;
+        }
+    }
+    double out[3];
+    block_sum_f64<PZ_TX * PZ_TY, 3>(sums, out);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const size_t nblk = gridDim.x;
+        partials[blockIdx.x] = out[0];
+        partials[nblk + blockIdx.x] = out[1];
+        partials[2 * nblk + blockIdx.x] = out[2];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ls_init(LSState *ls, cudaStream_t st) {
+    k_ls_init<<<1, 1, 0, st>>>(ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond,
+                             cudaStream_t st) {
+    k_ls_decide<<<1, 1, 0, st>>>(ls, sc, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prox_zi_dev(const void *vol, ZLayout L, const float *gzi, const LSState *ls,
+                               void *trial, int dtype, double *partials, int *n_partials,
+                               cudaStream_t st) {
+    const int nb = prox_zi_num_partials(L.nx, L.ny, L.nz);
+    if (n_partials) *n_partials = nb;
+    dim3 block(PZ_TX, PZ_TY);
+    switch (dtype) {
+        case FBL_BF16:
+            k_prox_zi_dev<<<nb, block, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, ls,
+                                                (__nv_bfloat16 *)trial, partials);
+            break;
+        case FBL_F16:
+            k_prox_zi_dev<<<nb, block, 0, st>>>((const __half *)vol, L, gzi, ls, (__half *)trial,
+                                                partials);
+            break;
+        default:
+            k_prox_zi_dev<<<nb, block, 0, st>>>((const float *)vol, L, gzi, ls, (float *)trial,
+                                                partials);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fbl

@@ -163,6 +163,31 @@ __global__ void __launch_bounds__(F_NT) k_prox_flat(const T *__restrict__ x,
     }
 }
 
+// sum |x|, sum (x - xr)^2, sum xr^2 (xr may be NULL: the last two are 0)
+template <typename T>
+__global__ void __launch_bounds__(F_NT) k_norms(const T *__restrict__ x, const T *__restrict__ xr,
+                                                int64_t n, double *__restrict__ partials) {
+    float sums[3] = {0.f, 0.f, 0.f};
+    const int64_t stride = (int64_t)gridDim.x * F_NT;
+    for (int64_t e = (int64_t)blockIdx.x * F_NT + threadIdx.x; e < n; e += stride) {
+        const float v = to_f32(x[e]);
+        sums[0] += fabsf(v);
+        if (xr) {
+            const float r = to_f32(xr[e]);
+            const float d = v - r;
+            sums[1] = fmaf(d, d, sums[1]);
+            sums[2] = fmaf(r, r, sums[2]);
+        }
+    }
+    double out[3];
+    block_sum_f64<F_NT, 3>(sums, out);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = out[0];
+        partials[gridDim.x + blockIdx.x] = out[1];
+        partials[2 * gridDim.x + blockIdx.x] = out[2];
+    }
+}
+
 constexpr int R_NT = 1024;
 
 __global__ void __launch_bounds__(R_NT) k_reduce(const double *__restrict__ partials, int n,
@@ -285,6 +310,22 @@ cudaError_t launch_prox_flat_grid(const void *x, const float *gr, int64_t n, flo
             k_prox_flat<<<nb, F_NT, 0, st>>>((const float *)x, gr, n, alpha, amu, (float *)xbar,
                                              partials);
             break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms(const void *x, const void *xr, int dtype, int64_t n, double *partials,
+                         int *n_partials, cudaStream_t st) {
+    const int nb = flat_blocks(n);
+    if (n_partials) *n_partials = nb;
+    switch (dtype) {
+        case FBL_BF16:
+            k_norms<<<nb, F_NT, 0, st>>>((const __nv_bfloat16 *)x, (const __nv_bfloat16 *)xr, n, partials);
+            break;
+        case FBL_F16:
+            k_norms<<<nb, F_NT, 0, st>>>((const __half *)x, (const __half *)xr, n, partials);
+            break;
+        default: k_norms<<<nb, F_NT, 0, st>>>((const float *)x, (const float *)xr, n, partials); break;
     }
     return cudaGetLastError();
 }

@@ -215,3 +215,19 @@ def test_nonfinite_data_reported(fbl):
     xd = cuda(np.zeros(g.vol_shape, np.float32))
     rc, st = S.step_raw(xd, cuda(b))
     assert rc == 6
+
+
+def test_evaluate_full_objective_and_relative_error(fbl):
+    g = synth.WORKLOADS["c1_64"].geom
+    xt, b = problem(g, seed=12)
+    rng = np.random.default_rng(12)
+    x = np.maximum(xt + 0.05 * rng.standard_normal(g.vol_shape), 0).astype(np.float32)
+    G = fbl.geometry_create(g)
+    b32 = b.astype(np.float32)
+    F, fid, re = fbl.evaluate(G, cuda(x), cuda(b32), 0.7, x_true=cuda(xt.astype(np.float32)))
+    Fo = fblisa.full_objective(g, x.astype(np.float64), b32.astype(np.float64), 0.7)
+    assert F == pytest.approx(Fo, rel=2e-5)
+    xt32 = xt.astype(np.float32).astype(np.float64)
+    assert re == pytest.approx(np.linalg.norm(x - xt32) / np.linalg.norm(xt32), rel=1e-5)
+    Fh, fidh, reh = fbl.evaluate(G, x, b32, 0.7)  # host buffers, no reference volume
+    assert Fh == pytest.approx(F, rel=1e-12) and reh == 0.0
