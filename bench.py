@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time BF16/FP16 storage")
     ap.add_argument("--variant-steps", type=int, default=5)
+    ap.add_argument("--tto-epochs", type=int, default=10,
+                    help="epochs of plain FP32 that define F* (0: skip time-to-objective)")
+    ap.add_argument("--tto-check", type=int, default=3, help="iterations between F evaluations")
     return ap.parse_args()
 
 
@@ -205,6 +208,68 @@ def active_samples(g, views):
     return total
 
 
+def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
+    """Wall time (sum of CUDA-event step times; objective evaluations off the
+    clock) for plain FP32 FB-LISA and for learned proposal + BF16 storage +
+    graph capture to reach F(x) <= F* (1 + 1e-3), where F* is the plain
+    method's full objective after `epochs` epochs."""
+    import torch
+    from paper_2605_12085_gb300 import proposal
+    params, meta = proposal.load()
+    stream = torch.cuda.current_stream(device)
+    b16 = b.to(torch.bfloat16)
+
+    def run(fast, max_epochs, target=None):
+        p = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
+                               x_dtype=fbl.BF16 if fast else fbl.F32,
+                               b_dtype=fbl.BF16 if fast else fbl.F32,
+                               use_graph=1 if fast else 0, proposal=1 if fast else 0,
+                               autotune=1)
+        S = fbl.fblisa_create(G, p)
+        if fast:
+            S.set_proposal(params)
+        x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32,
+                        device=device)
+        bb = b16 if fast else b
+        elapsed, hist, k, trials = 0.0, [], 0, 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n_iter = sum(it for _, it in fbl.fbl_schedule(g.n_views, wl.N0, g.n_views, 1.0, 0.99,
+                                                        max_epochs))
+        while k < n_iter:
+            e0.record(stream)
+            st = S.step(x, bb)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            elapsed += e0.elapsed_time(e1) * 1e-3
+            k += 1
+            trials += st["backtracks"] + 1
+            if k % check_every == 0 or k == n_iter:
+                F = fbl.evaluate(G, x, b, wl.mu)[0]
+                hist.append((k, elapsed, F))
+                if target is not None and F <= target:
+                    break
+        return hist, trials / max(k, 1)
+
+    plain, plain_trials = run(False, epochs)
+    F_star = plain[-1][2]
+    target = F_star * (1.0 + 1e-3)
+    plain_hit = next(h for h in plain if h[2] <= target)
+    fast, fast_trials = run(True, 2 * epochs, target)
+    fast_hit = next((h for h in fast if h[2] <= target), None)
+    out = {"F_star": F_star, "rel_tol": 1e-3, "epochs_for_F_star": epochs,
+           "plain_fp32_s": plain_hit[1], "plain_iterations": plain_hit[0],
+           "plain_trials_per_iteration": plain_trials,
+           "fast": "learned proposal + BF16 storage + graph-captured iteration",
+           "fast_s": fast_hit[1] if fast_hit else None,
+           "fast_iterations": fast_hit[0] if fast_hit else None,
+           "fast_trials_per_iteration": fast_trials,
+           "speedup": (plain_hit[1] / fast_hit[1]) if fast_hit else None,
+           "check_every_iterations": check_every,
+           "proposal_traces": meta.get("traces")}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -327,6 +392,10 @@ def run_ours(args, rank, world, local_rank):
                               "backtracks_per_step": statistics.mean(st["backtracks"] for st in stv)}
             del Sv, xv, bv
         out["variants"] = variants
+
+    if args.tto_epochs > 0 and rank == 0:
+        out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,
+                                                     args.tto_check)
 
     # end to end through the same C-ABI call with host (pinned) buffers
     if args.e2e_steps > 0:

@@ -96,7 +96,8 @@ typedef struct {
     int32_t N0;               /* initial mini-batch size N_0 (Sec. 3: 8) */
     int32_t n_max;            /* largest mini-batch, 0 = n_views */
     int32_t max_backtracks;   /* cap on step reductions per iteration */
-    int32_t proposal;         /* 0: reset alpha to alpha_0 (Step 2d); 1: learned proposal */
+    int32_t proposal;         /* 0: reset alpha to alpha_0 (Step 2d); 1: learned proposal
+                                 (set the network with fblisa_set_proposal) */
     uint64_t seed;            /* mini-batch permutation seed */
     int32_t x_dtype;          /* fbl_dtype of the caller's x and the solver's iterates */
     int32_t b_dtype;          /* fbl_dtype of the caller's b */
@@ -121,6 +122,10 @@ typedef struct {
     double gTd;               /* grad f_N(x)^T (x_bar - x) */
     double dnorm2;            /* ||x_bar - x||^2 */
     double margin;            /* rhs of (2.3) minus f_N(x_bar), >= 0 when accepted */
+    double grad_norm2;        /* ||grad f_N(x)||^2 */
+    int32_t j_start;          /* first trial was alpha_0 * beta^j_start (0 without proposal) */
+    float pred;               /* the proposal network's output (0 without proposal) */
+    float features[8];        /* the proposal's inputs at this iteration (always recorded) */
 } fbl_step_stats;
 
 /* Defaults: alpha0 1e-3, beta 0.5, mu 1, C 1, eps_base 0.99, N0 8, n_max 0,
@@ -238,6 +243,25 @@ FBL_API fbl_status prox_reduce_static(const void *x, int32_t x_dtype, const floa
                                       void *stream);
 
 /*
+ * The learned step proposal's network (no counterpart in the paper, which
+ * resets the step to alpha_0 at every iteration, Step 2d): a perceptron
+ * 8 -> 64 -> 64 -> 1 with tanh hidden units, FP32, parameters packed as
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3 (FBL_MLP_PARAMS floats).
+ * Loss: 1/(2n) sum_s (y_s - t_s)^2.  All arrays are device memory; X is
+ * [n][8].  mlp_gradient writes the full-batch gradient and *loss_host;
+ * mlp_train runs `epochs` passes of Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+ * over consecutive minibatches of `batch` samples, updating params, the
+ * moment arrays and the device step counter *adam_step.
+ */
+enum { FBL_MLP_INPUTS = 8, FBL_MLP_HIDDEN = 64, FBL_MLP_PARAMS = 4801 };
+FBL_API fbl_status mlp_forward(const float *params, const float *X, int32_t n, float *y, void *stream);
+FBL_API fbl_status mlp_gradient(const float *params, const float *X, const float *t, int32_t n,
+                                float *grad, double *loss_host, void *stream);
+FBL_API fbl_status mlp_train(float *params, float *adam_m, float *adam_v, int32_t *adam_step,
+                             const float *X, const float *t, int32_t n, int32_t batch,
+                             int32_t epochs, float lr, double *last_loss_host, void *stream);
+
+/*
  * fblisa_create -- a solver for Algorithm 1 on geometry g with the given
  * hyperparameters; owns its scratch (gradient, trial point, residual,
  * reduction slots) and its schedule/mini-batch state (Step 1, Step 2a).
@@ -266,6 +290,21 @@ FBL_API fbl_status fblisa_step(fbl_solver *s, void *x, const void *b, fbl_step_s
  */
 FBL_API fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t epochs,
                       fbl_step_stats *trace, int64_t trace_cap, int64_t *n_steps, void *stream);
+
+/*
+ * fblisa_set_proposal -- install the step-proposal network (FBL_MLP_PARAMS
+ * floats, host or device, copied) and switch the proposal on or off.  With
+ * the proposal on, the first trial of each iteration is alpha_0 * beta^j with
+ * j = clamp(round(net(features) - margin), 0, max_backtracks): a point of the
+ * plain rule's own step grid, chosen by the network trained to predict the
+ * number of backtracks the plain rule needs.  The test (2.3) and the
+ * backtracking are unchanged.  Features (fbl_step_stats.features): previous
+ * accepted grid index/10, log(f/f_prev), log(|g|/|g_prev|),
+ * log2(alpha_0 |g|^2 / (2 f))/10, N_t/n_theta, log(1+k)/10, 1 if there is a
+ * previous iteration, log10(f)/10, with f = f_N(x) and g = grad f_N(x).
+ */
+FBL_API fbl_status fblisa_set_proposal(fbl_solver *s, const float *params, float margin,
+                                       int32_t enable);
 
 /*
  * Per-kernel device time of a solver, for performance reporting: with

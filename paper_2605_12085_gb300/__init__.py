@@ -53,10 +53,14 @@ class fbl_step_stats(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("alpha_init", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("f_x", ctypes.c_double),
                 ("f_xbar", ctypes.c_double), ("gTd", ctypes.c_double),
-                ("dnorm2", ctypes.c_double), ("margin", ctypes.c_double)]
+                ("dnorm2", ctypes.c_double), ("margin", ctypes.c_double),
+                ("grad_norm2", ctypes.c_double), ("j_start", ctypes.c_int32),
+                ("pred", ctypes.c_float), ("features", ctypes.c_float * 8)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["features"] = list(self.features)
+        return d
 
 
 class fbl_tune_report(ctypes.Structure):
@@ -76,7 +80,8 @@ EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_
            "residual_norm", "prox_reduce", "fblisa_create", "fblisa_destroy", "fblisa_step",
            "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
            "fbl_epoch_batches", "prox_reduce_static", "geometry_autotune",
-           "geometry_set_launch", "evaluate"]
+           "geometry_set_launch", "evaluate", "mlp_forward", "mlp_gradient", "mlp_train",
+           "fblisa_set_proposal"]
 
 
 def _load():
@@ -98,12 +103,16 @@ def _load():
         "prox_reduce": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
         "prox_reduce_static": (st, [vp, i32, vp, i64, dbl, dbl, vp, P(dbl), vp]),
         "evaluate": (st, [vp, vp, i32, vp, i32, dbl, vp, P(dbl), vp]),
+        "mlp_forward": (st, [vp, vp, i32, vp, vp]),
+        "mlp_gradient": (st, [vp, vp, vp, i32, vp, P(dbl), vp]),
+        "mlp_train": (st, [vp, vp, vp, vp, vp, vp, i32, i32, i32, ctypes.c_float, P(dbl), vp]),
         "fblisa_create": (st, [vp, P(fbl_params), P(vp)]),
         "fblisa_destroy": (None, [vp]),
         "fblisa_step": (st, [vp, vp, vp, P(fbl_step_stats), vp]),
         "fblisa_run": (st, [vp, vp, vp, i32, P(fbl_step_stats), i64, P(i64), vp]),
         "fblisa_last_batch": (st, [vp, P(i32), i32, P(i32)]),
         "fblisa_profile": (st, [vp, i32, P(fbl_profile)]),
+        "fblisa_set_proposal": (st, [vp, vp, ctypes.c_float, i32]),
         "fbl_last_error": (ctypes.c_char_p, []),
         "fbl_schedule": (st, [i32, i32, i32, dbl, dbl, i32, P(i32), P(i32)]),
         "fbl_epoch_batches": (st, [ctypes.c_uint64, i32, i32, i32, P(i32)]),
@@ -300,6 +309,47 @@ def prox_reduce_static(x, g, alpha: float, mu: float, xbar, stream=None):
     return xbar, (out[0], out[1], out[2])
 
 
+MLP_PARAMS = 4801
+
+
+def mlp_forward(params, X, y=None, stream=None):
+    """y = net(X) for X [n][8] (CUDA tensors)."""
+    n = int(X.shape[0])
+    if y is None:
+        y = _like(X, (n,), F32)
+    _check(lib.mlp_forward(_ptr(params), _ptr(X), n, _ptr(y), _stream(params, X, stream=stream)))
+    return y
+
+
+def mlp_gradient(params, X, t, stream=None):
+    """(full-batch gradient of 1/(2n) sum (y - t)^2, loss) for CUDA tensors."""
+    n = int(X.shape[0])
+    g = _like(params, (MLP_PARAMS,), F32)
+    loss = ctypes.c_double()
+    _check(lib.mlp_gradient(_ptr(params), _ptr(X), _ptr(t), n, _ptr(g), ctypes.byref(loss),
+                            _stream(params, X, stream=stream)))
+    return g, loss.value
+
+
+class MlpTrainer:
+    """Adam state for training a parameter vector in place on the GPU."""
+
+    def __init__(self, params):
+        import torch
+        self.params = params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.step = torch.zeros(1, dtype=torch.int32, device=params.device)
+
+    def train(self, X, t, batch=256, epochs=1, lr=1e-3, stream=None) -> float:
+        loss = ctypes.c_double()
+        _check(lib.mlp_train(_ptr(self.params), _ptr(self.m), _ptr(self.v), _ptr(self.step),
+                             _ptr(X), _ptr(t), int(X.shape[0]), int(batch), int(epochs),
+                             float(lr), ctypes.byref(loss),
+                             _stream(self.params, X, stream=stream)))
+        return loss.value
+
+
 def params_default(**kw) -> fbl_params:
     p = fbl_params()
     lib.fbl_params_default(ctypes.byref(p))
@@ -352,6 +402,14 @@ class Solver:
         pr = fbl_profile()
         _check(lib.fblisa_profile(self.handle, int(bool(enable)), ctypes.byref(pr)))
         return {name: (pr.ms[c], pr.launches[c]) for c, name in enumerate(PROFILE_CLASSES)}
+
+    def set_proposal(self, params, margin: float = 0.5, enable: bool = True):
+        """Install the step-proposal network (4801 floats, tensor or array)."""
+        if params is None:
+            _check(lib.fblisa_set_proposal(self.handle, None, float(margin), int(bool(enable))))
+        else:
+            _check(lib.fblisa_set_proposal(self.handle, _ptr(params), float(margin),
+                                           int(bool(enable))))
 
     def last_batch(self):
         n = ctypes.c_int32()

@@ -4,6 +4,7 @@
 // numeric step runs in the kernels of k_project.cu, k_backproject.cu and
 // k_prox.cu; this file only prepares tables, moves data and makes the (2.3)
 // decision on four FP64 scalars.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -740,6 +741,11 @@ struct fbl_solver {
     cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams
     LSState *d_ls = nullptr;                      // line-search state (device)
     LSState *h_ls = nullptr;                      // its host copy (pinned)
+    // step proposal: statistics of the previous iteration and the network
+    PropState *d_ps = nullptr;
+    PropState *h_ps = nullptr;                    // pinned mirror (host-loop mode)
+    float *d_mlp = nullptr;                       // network parameters, NULL until set
+    float margin = 0.5f;
 };
 
 namespace {
@@ -764,6 +770,9 @@ void solver_free(fbl_solver *s) {
     if (s->cap2) cudaStreamDestroy(s->cap2);
     cudaFree(s->d_ls);
     cudaFreeHost(s->h_ls);
+    cudaFree(s->d_ps);
+    cudaFreeHost(s->h_ps);
+    cudaFree(s->d_mlp);
 }
 
 cudaEvent_t prof_event(fbl_solver *s) {
@@ -817,8 +826,9 @@ fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
         CK(cudaMemset(s->rt, 0, need * sizeof(float)), "residual buffer");  // zero row pads
         s->rt_cap = need;
     }
-    const size_t np = std::max((size_t)project_num_partials(s->g->dg, N),
-                               (size_t)3 * prox_zi_num_partials(d.nx, d.ny, d.nz));
+    const size_t np = std::max({(size_t)project_num_partials(s->dg, N),
+                                (size_t)3 * prox_zi_num_partials(d.nx, d.ny, d.nz),
+                                (size_t)backproject_num_partials(s->dg)});
     if (np > s->partials_cap) {
         drop_graphs(s);
         cudaFree(s->partials);
@@ -860,7 +870,10 @@ fbl_status build_graph(fbl_solver *s, fbl_solver::GraphEntry &ge) {
     cudaError_t e = launch_project(PROJ_RESID, s->dg, ge.st, s->L, xdt, s->d_views, N, ge.bd,
                                    s->p.b_dtype, ge.bmap, s->rt, FBL_F32, s->partials, &np, cs);
     if (e == cudaSuccess) e = launch_reduce(s->partials, np, np, 1, s->d_sc + 0, cs);
-    if (e == cudaSuccess) e = launch_backproject(s->dg, s->rt, s->d_views, N, scale, s->grad, cs);
+    if (e == cudaSuccess) e = launch_backproject(s->dg, s->rt, s->d_views, N, scale, s->grad, cs, s->partials);
+    const int nbp = backproject_num_partials(s->dg);
+    if (e == cudaSuccess) e = launch_reduce(s->partials, nbp, nbp, 1, s->d_sc + 5, cs);
+    if (e == cudaSuccess) e = launch_propose(s->d_ls, s->d_ps, s->d_sc, s->p.proposal ? s->d_mlp : nullptr, s->margin, cs);
     if (e == cudaSuccess) e = launch_ls_init(s->d_ls, cs);
     cudaStreamCaptureStatus cst;
     cudaGraph_t cg = nullptr;
@@ -887,7 +900,7 @@ fbl_status build_graph(fbl_solver *s, fbl_solver::GraphEntry &ge) {
                 eb = launch_project(PROJ_NORM, s->dg, ge.tr, s->L, xdt, s->d_views, N, ge.bd, s->p.b_dtype,
                                     ge.bmap, nullptr, FBL_F32, s->partials, &np2, cb);
             if (eb == cudaSuccess) eb = launch_reduce(s->partials, np2, np2, 1, s->d_sc + 4, cb);
-            if (eb == cudaSuccess) eb = launch_ls_decide(s->d_ls, s->d_sc, cond, cb);
+            if (eb == cudaSuccess) eb = launch_ls_decide(s->d_ls, s->d_ps, s->d_sc, cond, cb);
             cudaError_t ee = cudaStreamEndCapture(cb, &body);
             e = eb != cudaSuccess ? eb : ee;
         }
@@ -925,6 +938,10 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         if (new_epoch) s->epoch_views = save_views;
     };
     const int32_t N = s->N_t;
+    if (s->p.proposal && !s->d_mlp) {
+        restore();
+        return fail(FBL_E_INVAL, "fblisa_step: proposal enabled but no network set (fblisa_set_proposal)");
+    }
     fbl_status rc = ensure_batch_buffers(s, N);
     if (rc) {
         restore();
@@ -987,6 +1004,8 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         cfg.scale = scale;
         cfg.max_backtracks = s->p.max_backtracks;
         cfg.force_reject = s->p.force_reject;
+        cfg.N_t = N;
+        cfg.n_theta = d.n_views;
         *s->h_ls = cfg;
         CK(cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(LSState), cudaMemcpyHostToDevice, st), "line-search state");
         CK(cudaGraphLaunch(ge->exec, st), "graph launch");
@@ -997,7 +1016,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         s->prof_launches[2] += 1;
         s->prof_launches[1] += trials;
         s->prof_launches[3] += trials;
-        s->prof_launches[4] += 2 + 3 * trials;
+        s->prof_launches[4] += 4 + 3 * trials;
         const bool accepted = r.status == FBL_OK && r.accepted;
         if (stats) {
             stats->k = s->k;
@@ -1005,7 +1024,11 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
             stats->N_t = N;
             stats->backtracks = r.trials;
             stats->alpha = r.alpha;
-            stats->alpha_init = s->p.alpha0;
+            stats->alpha_init = r.alpha_init;
+            stats->j_start = r.j_start;
+            stats->pred = r.pred;
+            stats->grad_norm2 = r.g2;
+            for (int q = 0; q < MLP_IN; ++q) stats->features[q] = r.feat[q];
             stats->rho0 = r.rho0;
             stats->f_x = r.f_x;
             stats->f_xbar = r.f_xbar;
@@ -1037,11 +1060,35 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
        "reduce");
     CK(prof_launch(s, 2, st, [&] {
-           return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st);
+           return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials);
        }),
        "gradient kernel");
+    const int nbp = backproject_num_partials(s->dg);
+    CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, nbp, nbp, 1, s->d_sc + 5, st); }),
+       "reduce");
+    // first trial step: alpha_0 (Step 2d), or the learned proposal on the same grid
+    {
+        LSState cfg;
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.alpha_init = s->p.alpha0;
+        cfg.beta = s->p.beta;
+        cfg.mu = s->p.mu;
+        cfg.scale = scale;
+        cfg.max_backtracks = s->p.max_backtracks;
+        cfg.N_t = N;
+        cfg.n_theta = d.n_views;
+        *s->h_ls = cfg;
+    }
+    CK(cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(LSState), cudaMemcpyHostToDevice, st), "line-search state");
+    CK(prof_launch(s, 4, st, [&] {
+           return launch_propose(s->d_ls, s->d_ps, s->d_sc, s->p.proposal ? s->d_mlp : nullptr, s->margin, st);
+       }),
+       "proposal kernel");
+    CK(cudaMemcpyAsync(s->h_ls, s->d_ls, sizeof(LSState), cudaMemcpyDeviceToHost, st), "line-search state");
+    CK(cudaStreamSynchronize(st), "proposal");
+    const LSState prop = *s->h_ls;
     // Step 2c: backtracking on (2.3)
-    double alpha = s->p.alpha0;
+    double alpha = prop.alpha_init;
     const double alpha_init = alpha;
     const int64_t nvox = (int64_t)d.nx * d.ny * d.nz;
     (void)nvox;
@@ -1092,6 +1139,10 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         stats->backtracks = accepted ? bt : s->p.max_backtracks;
         stats->alpha = accepted ? alpha : alpha / s->p.beta;
         stats->alpha_init = alpha_init;
+        stats->j_start = prop.j_start;
+        stats->pred = prop.pred;
+        stats->grad_norm2 = prop.g2;
+        for (int q = 0; q < MLP_IN; ++q) stats->features[q] = prop.feat[q];
         stats->rho0 = rho0;
         stats->f_x = f_x;
         stats->f_xbar = f_xb;
@@ -1105,8 +1156,15 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         return fail(FBL_E_LINESEARCH, "fblisa_step: no step passed (2.3) within %d backtracks",
                     s->p.max_backtracks);
     }
-    // Step 2d: x <- x_bar (swap the state and trial buffers); alpha restarts from alpha_0.
+    // Step 2d: x <- x_bar (swap the state and trial buffers); the next first
+    // trial is alpha_0 again, or the proposal's
     std::swap(s->st, s->tr);
+    s->h_ps->f_prev = f_x;
+    s->h_ps->g2_prev = prop.g2;
+    s->h_ps->j_prev = prop.j_start + bt;
+    s->h_ps->have_prev = 1;
+    s->h_ps->k += 1;
+    CK(cudaMemcpyAsync(s->d_ps, s->h_ps, sizeof(PropState), cudaMemcpyHostToDevice, st), "proposal state");
     s->k += 1;
     s->iter_in_epoch += 1;
     return FBL_OK;
@@ -1273,6 +1331,53 @@ extern "C" fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_
     return autotune_devgeom(g, g->dg, x_dtype, n_sel, (cudaStream_t)stream, report);
 }
 
+extern "C" fbl_status mlp_forward(const float *params, const float *X, int32_t n, float *y, void *stream) {
+    if (!params || (n > 0 && (!X || !y)) || n < 0) return fail(FBL_E_INVAL, "mlp_forward: bad argument");
+    if (!is_device_ptr(params) || (n > 0 && (!is_device_ptr(X) || !is_device_ptr(y))))
+        return fail(FBL_E_INVAL, "mlp_forward: arrays must be device memory");
+    CK(launch_mlp_forward(params, X, n, y, (cudaStream_t)stream), "mlp forward");
+    return FBL_OK;
+}
+
+extern "C" fbl_status mlp_gradient(const float *params, const float *X, const float *t, int32_t n,
+                                   float *grad, double *loss_host, void *stream) {
+    if (!params || !X || !t || !grad || !loss_host || n < 1) return fail(FBL_E_INVAL, "mlp_gradient: bad argument");
+    if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(t) || !is_device_ptr(grad))
+        return fail(FBL_E_INVAL, "mlp_gradient: arrays must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    AsyncBuf loss;
+    CK(loss.alloc(sizeof(double), s), "mlp loss");
+    CK(launch_mlp_train(const_cast<float *>(params), nullptr, nullptr, X, t, n, n, 1, 0.f, 0, grad,
+                        (double *)loss.p, nullptr, s),
+       "mlp gradient");
+    CK(cudaMemcpyAsync(loss_host, loss.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    CK(cudaStreamSynchronize(s), "mlp_gradient");
+    return FBL_OK;
+}
+
+extern "C" fbl_status mlp_train(float *params, float *adam_m, float *adam_v, int32_t *adam_step,
+                                const float *X, const float *t, int32_t n, int32_t batch,
+                                int32_t epochs, float lr, double *last_loss_host, void *stream) {
+    if (!params || !adam_m || !adam_v || !adam_step || !X || !t || n < 1 || batch < 1 || epochs < 0 ||
+        !(lr > 0))
+        return fail(FBL_E_INVAL, "mlp_train: bad argument");
+    for (const void *p : {(const void *)params, (const void *)adam_m, (const void *)adam_v,
+                          (const void *)adam_step, (const void *)X, (const void *)t})
+        if (!is_device_ptr(p)) return fail(FBL_E_INVAL, "mlp_train: arrays must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    AsyncBuf loss;
+    CK(loss.alloc(sizeof(double), s), "mlp loss");
+    CK(cudaMemsetAsync(loss.p, 0, sizeof(double), s), "memset");
+    CK(launch_mlp_train(params, adam_m, adam_v, X, t, n, batch, epochs, lr, 1, nullptr,
+                        (double *)loss.p, adam_step, s),
+       "mlp train");
+    double l = 0.0;
+    CK(cudaMemcpyAsync(&l, loss.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    CK(cudaStreamSynchronize(s), "mlp_train");
+    if (last_loss_host) *last_loss_host = l;
+    return FBL_OK;
+}
+
 extern "C" fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                           int32_t k2_vpl) {
     if (!g) return fail(FBL_E_INVAL, "geometry_set_launch: null geometry");
@@ -1297,7 +1402,7 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     const int32_t n_max = p->n_max > 0 ? p->n_max : d.n_views;
     if (p->N0 < 1 || p->N0 > n_max || n_max > d.n_views)
         return fail(FBL_E_INVAL, "fblisa_create: need 1 <= N0 <= n_max <= n_views");
-    if (p->proposal != 0) return fail(FBL_E_UNSUPPORTED, "fblisa_create: learned proposal not available");
+    if (p->proposal != 0 && p->proposal != 1) return fail(FBL_E_INVAL, "fblisa_create: proposal must be 0 or 1");
     auto s = new fbl_solver();
     s->g = g;
     s->dg = g->dg;
@@ -1322,6 +1427,10 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_sc, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ls, sizeof(LSState));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_ls, sizeof(LSState));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ps, sizeof(PropState));
+    if (e == cudaSuccess) e = cudaMemset(s->d_ps, 0, sizeof(PropState));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_ps, sizeof(PropState));
+    if (e == cudaSuccess) std::memset(s->h_ps, 0, sizeof(PropState));
     if (e != cudaSuccess) {
         solver_free(s);
         delete s;
@@ -1396,6 +1505,23 @@ extern "C" fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t 
         return rc;
     }
     return st2;
+}
+
+extern "C" fbl_status fblisa_set_proposal(fbl_solver *s, const float *params, float margin,
+                                          int32_t enable) {
+    if (!s || (enable && !params)) return fail(FBL_E_INVAL, "fblisa_set_proposal: null argument");
+    if (!std::isfinite(margin)) return fail(FBL_E_INVAL, "fblisa_set_proposal: bad margin");
+    fbl_status st = check_device(s->device);
+    if (st) return st;
+    if (params) {
+        if (!s->d_mlp) CK(cudaMalloc(&s->d_mlp, MLP_PARAMS * sizeof(float)), "proposal network");
+        CK(cudaMemcpy(s->d_mlp, params, MLP_PARAMS * sizeof(float), cudaMemcpyDefault), "proposal network");
+        drop_graphs(s);  // graphs captured without the network
+    }
+    s->margin = margin;
+    if (s->p.proposal != (enable ? 1 : 0)) drop_graphs(s);
+    s->p.proposal = enable ? 1 : 0;
+    return FBL_OK;
 }
 
 extern "C" fbl_status fblisa_profile(fbl_solver *s, int32_t enable, fbl_profile *out) {

@@ -156,9 +156,12 @@ int project_num_partials(const DevGeom &g, int n_sel);
 cudaError_t launch_weight(const DevGeom &g, const void *y, int y_dtype, const int32_t *views,
                           int n_sel, float *rt, cudaStream_t st);
 
-// gzi[j][i][k] = scale * sum over listed views of the transpose taps of rt.
+// gzi[j][i][k] = scale * sum over listed views of the transpose taps of rt;
+// with g2_partials, also the per-block sums of gzi^2 (backproject_num_partials).
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
-                               int n_sel, float scale, float *gzi, cudaStream_t st);
+                               int n_sel, float scale, float *gzi, cudaStream_t st,
+                               double *g2_partials = nullptr);
+int backproject_num_partials(const DevGeom &g);
 
 // x_bar = max(x - alpha*g - alpha*mu, 0) on the solver's state: reads vol
 // (current x) and gzi, writes trial; partials[3][nblk] =
@@ -184,18 +187,48 @@ cudaError_t launch_prox_flat_grid(const void *x, const float *gr, int64_t n, flo
 cudaError_t launch_norms(const void *x, const void *xr, int dtype, int64_t n, double *partials,
                          int *n_partials, cudaStream_t st);
 
-// Line-search state of one graph-captured iteration (device memory).
+// The step-proposal network (k_mlp.cu): 8 -> 64 -> 64 -> 1, tanh, FP32.
+constexpr int MLP_IN = 8;
+constexpr int MLP_HIDDEN = 64;
+constexpr int MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN +
+                           MLP_HIDDEN + 1;  // 4801
+constexpr int MLP_PARAMS_PAD = (MLP_PARAMS + 3) / 4 * 4;
+size_t mlp_train_smem();
+cudaError_t launch_mlp_forward(const float *params, const float *X, int n, float *y, cudaStream_t st);
+// mode 0: full-batch gradient and loss; mode 1: Adam epochs over minibatches.
+cudaError_t launch_mlp_train(float *params, float *adam_m, float *adam_v, const float *X,
+                             const float *T, int n, int batch, int epochs, float lr, int mode,
+                             float *grad_out, double *loss_out, int *step_io, cudaStream_t st);
+
+// Line-search state of one iteration (device memory).
 struct LSState {
     double alpha_init, alpha, beta, mu, scale;  // scale = n_theta / N_t
-    double rho0, gTd, dd, rho1, f_x, f_xbar, rhs;
-    int trials, max_backtracks, accepted, status, force_reject, pad;
+    double rho0, gTd, dd, rho1, f_x, f_xbar, rhs, g2;
+    int trials, max_backtracks, accepted, status, force_reject;
+    int j_start;                // first trial = alpha0 * beta^j_start
+    int N_t, n_theta;
+    float pred;                 // network output (backtracks predicted)
+    float feat[MLP_IN];         // the proposal's input features
 };
 
+// Statistics carried from one accepted iteration to the next (device memory).
+struct PropState {
+    double f_prev, g2_prev;
+    long long k;
+    int j_prev, have_prev;
+};
+
+// Features of this iteration from sc[0] = rho0 and sc[5] = ||grad f_N||^2,
+// then (params != NULL) the network's prediction and the first trial step
+// alpha0 * beta^j; without params the first trial is alpha0 (Step 2d).
+cudaError_t launch_propose(LSState *ls, const PropState *ps, const double *sc, const float *params,
+                           float margin, cudaStream_t st);
 cudaError_t launch_ls_init(LSState *ls, cudaStream_t st);
-// Evaluate (2.3) on sc = [rho0, gTd, dd, l1, rho1]; accept, or shrink the step
-// and request another trial (the WHILE condition), or stop with a status.
-cudaError_t launch_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond,
-                             cudaStream_t st);
+// Evaluate (2.3) on sc = [rho0, gTd, dd, l1, rho1]; accept (and record the
+// iteration in ps), or shrink the step and request another trial (the WHILE
+// condition), or stop with a status.
+cudaError_t launch_ls_decide(LSState *ls, PropState *ps, const double *sc,
+                             cudaGraphConditionalHandle cond, cudaStream_t st);
 // launch_prox_zi with alpha and mu read from the line-search state.
 cudaError_t launch_prox_zi_dev(const void *vol, ZLayout L, const float *gzi, const LSState *ls,
                                void *trial, int dtype, double *partials, int *n_partials,

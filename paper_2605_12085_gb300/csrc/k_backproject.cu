@@ -23,6 +23,7 @@
 // lanes' row reads are contiguous and need no bounds test.  The gradient is
 // written in z-innermost order [j][i][k], coalesced.
 #include "fbl_internal.cuh"
+#include "fbl_reduce.cuh"
 
 namespace fbl {
 namespace {
@@ -37,6 +38,7 @@ struct BpArgs {
     int n_sel;
     float scale;
     float *gzi;
+    double *g2_partials;  // optional: per-block sum of the squared gradient
 };
 
 template <int NTAP, int K2_VPL>
@@ -47,17 +49,17 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
     const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
     const int j = blockIdx.y;
     const int kfirst = blockIdx.z * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+3
-    if (i >= g.nx) return;
     float acc[K2_VPL];
 #pragma unroll
     for (int q = 0; q < K2_VPL; ++q) acc[q] = 0.f;
     const float xc = ((float)i - g.cx) * g.vx;
     const float yc = ((float)j - g.cy) * g.vy;
     const int rp = rt_pitch(g.nv);
+    const int nsel = i < g.nx ? a.n_sel : 0;  // a warp past the volume edge only joins the block sum
     const int lo_max = g.nv + RT_PAD - NTAP;  // last first-row whose taps stay in the pad
     const long long kfirst_fx = (long long)kfirst << FX_BITS;
     constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
-    for (int s = 0; s < a.n_sel; ++s) {
+    for (int s = 0; s < nsel; ++s) {
         const int v = a.views[s];
         const float2 cs = g.trig[v];
         const float xi = xc * cs.x + yc * cs.y;
@@ -114,19 +116,40 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
             }
         }
     }
-    float *out = a.gzi + ((size_t)j * g.nx + i) * g.nz;
+    float g2 = 0.f;
+    if (i < g.nx) {
+        float *out = a.gzi + ((size_t)j * g.nx + i) * g.nz;
 #pragma unroll
-    for (int q = 0; q < K2_VPL; ++q) {
-        const int k = kfirst + q;
-        if (k < g.nz) out[k] = a.scale * acc[q];
+        for (int q = 0; q < K2_VPL; ++q) {
+            const int k = kfirst + q;
+            if (k < g.nz) {
+                const float val = a.scale * acc[q];
+                out[k] = val;
+                g2 = fmaf(val, val, g2);
+            }
+        }
+    }
+    if (a.g2_partials) {
+        float vv[1] = {g2};
+        double o[1];
+        block_sum_f64<K2_LANES * K2_WARPS, 1>(vv, o);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            a.g2_partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = o[0];
     }
 }
 
 }  // namespace
 
+int backproject_num_partials(const DevGeom &g) {
+    const int vpl = g.k2_vpl == 2 ? 2 : 4;
+    return ((g.nx + K2_WARPS - 1) / K2_WARPS) * g.ny * ((g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
+}
+
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
-                               int n_sel, float scale, float *gzi, cudaStream_t st) {
+                               int n_sel, float scale, float *gzi, cudaStream_t st,
+                               double *g2_partials) {
     BpArgs a;
+    a.g2_partials = g2_partials;
     a.g = g;
     a.rt = rt;
     a.views = views;

@@ -20,8 +20,71 @@ __global__ void k_ls_init(LSState *ls) {
     ls->status = FBL_OK;
 }
 
+// Input features of the step proposal (all scale-free), from this
+// iteration's f_N(x) and ||grad f_N(x)||^2 and the previous accepted one.
+__device__ void proposal_features(const LSState &ls, const PropState &ps, double f, double g2,
+                                  float *feat) {
+    const bool have = ps.have_prev != 0;
+    feat[0] = have ? 0.1f * (float)ps.j_prev : 0.f;
+    feat[1] = have ? (float)log(fmax(f, 1e-300) / fmax(ps.f_prev, 1e-300)) : 0.f;
+    feat[2] = have ? (float)(0.5 * log(fmax(g2, 1e-300) / fmax(ps.g2_prev, 1e-300))) : 0.f;
+    feat[3] = (float)(0.1 * log2(fmax(ls.alpha_init * g2 / fmax(2.0 * f, 1e-300), 1e-300)));
+    feat[4] = (float)ls.N_t / (float)ls.n_theta;
+    feat[5] = (float)(0.1 * log(1.0 + (double)ps.k));
+    feat[6] = have ? 1.f : 0.f;
+    feat[7] = (float)(0.1 * log10(fmax(f, 1e-300)));
+}
+
+// One warp: features, the network (hidden units l and l+32 per lane), the
+// first trial step.  ls->alpha_init holds alpha_0 on entry.
+__global__ void k_propose(LSState *ls, const PropState *ps, const double *sc, const float *params,
+                          float margin) {
+    __shared__ float x[MLP_IN], h1[MLP_HIDDEN];
+    const int lane = threadIdx.x;
+    const double rho0 = sc[0], g2 = sc[5];
+    const double f = __dmul_rn(__dmul_rn(0.5, ls->scale), rho0);
+    if (lane == 0) proposal_features(*ls, *ps, f, g2, x);
+    __syncwarp();
+    float pred = 0.f;
+    if (params) {
+        constexpr int NI = MLP_IN, NH = MLP_HIDDEN;
+        constexpr int OB1 = NH * NI, OW2 = OB1 + NH, OB2 = OW2 + NH * NH, OW3 = OB2 + NH, OB3 = OW3 + NH;
+        float z[2];
+        for (int h = 0; h < 2; ++h) {
+            const int u = lane + 32 * h;
+            float a = params[OB1 + u];
+            for (int q = 0; q < NI; ++q) a = fmaf(params[u * NI + q], x[q], a);
+            z[h] = tanhf(a);
+        }
+        h1[lane] = z[0];
+        h1[lane + 32] = z[1];
+        __syncwarp();
+        float part = 0.f;
+        for (int h = 0; h < 2; ++h) {
+            const int u = lane + 32 * h;
+            float a = params[OB2 + u];
+            for (int v = 0; v < NH; ++v) a = fmaf(params[OW2 + u * NH + v], h1[v], a);
+            part = fmaf(params[OW3 + u], tanhf(a), part);
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        pred = part + params[OB3];
+    }
+    if (lane == 0) {
+        int j = 0;
+        if (params && isfinite(pred)) j = min(max((int)rintf(pred - margin), 0), ls->max_backtracks);
+        double a = ls->alpha_init;
+        for (int q = 0; q < j; ++q) a = __dmul_rn(a, ls->beta);  // the plain rule's step grid
+        ls->alpha_init = a;
+        ls->j_start = j;
+        ls->pred = pred;
+        ls->g2 = g2;
+        for (int q = 0; q < MLP_IN; ++q) ls->feat[q] = x[q];
+    }
+}
+
 // sc: [rho0, gTd, dd, l1, rho1] as reduced by the preceding kernels.
-__global__ void k_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond) {
+__global__ void k_ls_decide(LSState *ls, PropState *ps, const double *sc,
+                            cudaGraphConditionalHandle cond) {
     const double rho0 = sc[0], gTd = sc[1], dd = sc[2], rho1 = sc[4];
     const double alpha = ls->alpha;
     const double half_scale = __dmul_rn(0.5, ls->scale);
@@ -40,6 +103,11 @@ __global__ void k_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalH
         ls->status = FBL_E_NONFINITE;
     } else if (!ls->force_reject && f_xb <= rhs) {
         ls->accepted = 1;
+        ps->f_prev = f_x;
+        ps->g2_prev = ls->g2;
+        ps->j_prev = ls->j_start + ls->trials;
+        ps->have_prev = 1;
+        ps->k += 1;
     } else if (ls->trials >= ls->max_backtracks) {
         ls->status = FBL_E_LINESEARCH;
     } else {
@@ -99,9 +167,15 @@ cudaError_t launch_ls_init(LSState *ls, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_decide(LSState *ls, const double *sc, cudaGraphConditionalHandle cond,
-                             cudaStream_t st) {
-    k_ls_decide<<<1, 1, 0, st>>>(ls, sc, cond);
+cudaError_t launch_ls_decide(LSState *ls, PropState *ps, const double *sc,
+                             cudaGraphConditionalHandle cond, cudaStream_t st) {
+    k_ls_decide<<<1, 1, 0, st>>>(ls, ps, sc, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propose(LSState *ls, const PropState *ps, const double *sc, const float *params,
+                           float margin, cudaStream_t st) {
+    k_propose<<<1, 32, 0, st>>>(ls, ps, sc, params, margin);
     return cudaGetLastError();
 }
 
