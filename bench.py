@@ -227,7 +227,7 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
                                autotune=1)
         S = fbl.fblisa_create(G, p)
         if fast:
-            S.set_proposal(params)
+            S.set_proposal(params, margin=0.25)
         x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32,
                         device=device)
         bb = b16 if fast else b
@@ -265,7 +265,7 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
            "fast_iterations": fast_hit[0] if fast_hit else None,
            "fast_trials_per_iteration": fast_trials,
            "speedup": (plain_hit[1] / fast_hit[1]) if fast_hit else None,
-           "check_every_iterations": check_every,
+           "check_every_iterations": check_every, "proposal_margin": 0.25,
            "proposal_traces": meta.get("traces")}
     return out
 

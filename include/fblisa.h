@@ -147,7 +147,7 @@ FBL_API void geometry_destroy(fbl_geometry *g);
 /* Launch configurations tried by the autotuner and their measured times. */
 typedef struct {
     float k1_ms[4];     /* projector, (cols, split) = (8,1), (8,0), (4,1), (4,0) */
-    float k2_ms[2];     /* backprojector, voxels per lane = 4, 2 */
+    float k2_ms[4];     /* backprojector, voxels per lane = 4, 2, 8, 16 */
     int32_t k1_cols, k1_split, k2_vpl;  /* the chosen configuration */
 } fbl_tune_report;
 
@@ -162,7 +162,7 @@ FBL_API fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n
                                      fbl_tune_report *report);
 
 /* Set the launch configuration by hand: k1_cols in {4, 8}, k1_split in {0, 1},
- * k2_vpl in {2, 4}; FBL_E_INVAL otherwise. */
+ * k2_vpl in {2, 4, 8, 16}; FBL_E_INVAL otherwise. */
 FBL_API fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                        int32_t k2_vpl);
 
@@ -295,13 +295,21 @@ FBL_API fbl_status fblisa_run(fbl_solver *s, void *x, const void *b, int32_t epo
  * fblisa_set_proposal -- install the step-proposal network (FBL_MLP_PARAMS
  * floats, host or device, copied) and switch the proposal on or off.  With
  * the proposal on, the first trial of each iteration is alpha_0 * beta^j with
- * j = clamp(round(net(features) - margin), 0, max_backtracks): a point of the
- * plain rule's own step grid, chosen by the network trained to predict the
- * number of backtracks the plain rule needs.  The test (2.3) and the
- * backtracking are unchanged.  Features (fbl_step_stats.features): previous
- * accepted grid index/10, log(f/f_prev), log(|g|/|g_prev|),
- * log2(alpha_0 |g|^2 / (2 f))/10, N_t/n_theta, log(1+k)/10, 1 if there is a
- * previous iteration, log10(f)/10, with f = f_N(x) and g = grad f_N(x).
+ * j = clamp(floor(j_prev + net(features) + 1/2 - margin), 0, max_backtracks),
+ * j_prev the grid index of the previous accepted step (0 at the first
+ * iteration): a point of the plain rule's own step grid, chosen by the
+ * network trained to predict how the index the plain rule needs changes from
+ * one iteration to the next.  The test (2.3) and the backtracking are
+ * unchanged.  Features (fbl_step_stats.features), with f = f_N(x),
+ * g = grad f_N(x) and the curvature index c = log2(alpha_0 |g|^2 / (2 f)):
+ * c/10 at the first iteration (0 afterwards), log(f/f_prev),
+ * log(|g|/|g_prev|), (c - c_prev)/10, N_t/n_theta, log(1+k)/10, 1 if there is
+ * a previous iteration, (j_prev - j_prevprev)/4 -- only relative quantities
+ * once there is a previous iteration, so that a network trained on small
+ * volumes transfers to large ones.  margin (finite; 0.25 recommended) trades
+ * extra first trials (larger margin) against steps below the plain rule's
+ * (smaller margin).  Copies params before returning; FBL_E_INVAL on a null
+ * solver or a non-finite margin.
  */
 FBL_API fbl_status fblisa_set_proposal(fbl_solver *s, const float *params, float margin,
                                        int32_t enable);

@@ -64,7 +64,7 @@ class fbl_step_stats(ctypes.Structure):
 
 
 class fbl_tune_report(ctypes.Structure):
-    _fields_ = [("k1_ms", ctypes.c_float * 4), ("k2_ms", ctypes.c_float * 2),
+    _fields_ = [("k1_ms", ctypes.c_float * 4), ("k2_ms", ctypes.c_float * 4),
                 ("k1_cols", ctypes.c_int32), ("k1_split", ctypes.c_int32),
                 ("k2_vpl", ctypes.c_int32)]
 
@@ -403,7 +403,7 @@ class Solver:
         _check(lib.fblisa_profile(self.handle, int(bool(enable)), ctypes.byref(pr)))
         return {name: (pr.ms[c], pr.launches[c]) for c, name in enumerate(PROFILE_CLASSES)}
 
-    def set_proposal(self, params, margin: float = 0.5, enable: bool = True):
+    def set_proposal(self, params, margin: float = 0.25, enable: bool = True):
         """Install the step-proposal network (4801 floats, tensor or array)."""
         if params is None:
             _check(lib.fblisa_set_proposal(self.handle, None, float(margin), int(bool(enable))))

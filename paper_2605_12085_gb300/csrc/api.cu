@@ -745,7 +745,7 @@ struct fbl_solver {
     PropState *d_ps = nullptr;
     PropState *h_ps = nullptr;                    // pinned mirror (host-loop mode)
     float *d_mlp = nullptr;                       // network parameters, NULL until set
-    float margin = 0.5f;
+    float margin = 0.25f;
 };
 
 namespace {
@@ -1161,6 +1161,8 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     std::swap(s->st, s->tr);
     s->h_ps->f_prev = f_x;
     s->h_ps->g2_prev = prop.g2;
+    s->h_ps->dj_prev = prop.j_start + bt - s->h_ps->j_prev;
+    s->h_ps->have_dj = s->h_ps->have_prev;
     s->h_ps->j_prev = prop.j_start + bt;
     s->h_ps->have_prev = 1;
     s->h_ps->k += 1;
@@ -1287,7 +1289,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
         }
     best = 1e30f;
     qi = 0;
-    for (int vpl : {4, 2}) {
+    for (int vpl : {4, 2, 8, 16}) {
         DevGeom t = dg;
         t.k2_vpl = vpl;
         float ms = 0.f;
@@ -1302,7 +1304,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
             cudaEventDestroy(e1);
             return cuda_fail(e, "autotune backprojector");
         }
-        if (rep && qi < 2) rep->k2_ms[qi] = ms;
+        if (rep && qi < 4) rep->k2_ms[qi] = ms;
         ++qi;
         if (ms < best) {
             best = ms;
@@ -1381,8 +1383,10 @@ extern "C" fbl_status mlp_train(float *params, float *adam_m, float *adam_v, int
 extern "C" fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                           int32_t k2_vpl) {
     if (!g) return fail(FBL_E_INVAL, "geometry_set_launch: null geometry");
-    if ((k1_cols != 4 && k1_cols != 8) || (k1_split != 0 && k1_split != 1) || (k2_vpl != 2 && k2_vpl != 4))
-        return fail(FBL_E_INVAL, "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1}, k2_vpl in {2,4}");
+    if ((k1_cols != 4 && k1_cols != 8) || (k1_split != 0 && k1_split != 1) ||
+        (k2_vpl != 2 && k2_vpl != 4 && k2_vpl != 8 && k2_vpl != 16))
+        return fail(FBL_E_INVAL,
+                    "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1}, k2_vpl in {2,4,8,16}");
     g->dg.k1_cols = k1_cols;
     g->dg.k1_split = k1_split;
     g->dg.k2_vpl = k2_vpl;
@@ -1518,6 +1522,7 @@ extern "C" fbl_status fblisa_set_proposal(fbl_solver *s, const float *params, fl
         CK(cudaMemcpy(s->d_mlp, params, MLP_PARAMS * sizeof(float), cudaMemcpyDefault), "proposal network");
         drop_graphs(s);  // graphs captured without the network
     }
+    if (margin != s->margin) drop_graphs(s);  // captured graphs hold the margin as an argument
     s->margin = margin;
     if (s->p.proposal != (enable ? 1 : 0)) drop_graphs(s);
     s->p.proposal = enable ? 1 : 0;

@@ -215,7 +215,7 @@ struct LSState {
 struct PropState {
     double f_prev, g2_prev;
     long long k;
-    int j_prev, have_prev;
+    int j_prev, have_prev, dj_prev, have_dj;
 };
 
 // Features of this iteration from sc[0] = rho0 and sc[5] = ||grad f_N||^2,

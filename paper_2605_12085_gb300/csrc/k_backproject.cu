@@ -8,8 +8,9 @@
 // detector column, wz from the vertical crossing q_z(m) of its row.
 //
 // Work decomposition.  A warp owns 32*VPL voxels of one (i, j) column along z
-// (lane l holds the VPL consecutive voxels k0 + VPL*l ...; VPL = 2 or 4,
-// chosen by the autotuner).  Everything that depends only on
+// (lane l holds the VPL consecutive voxels k0 + VPL*l ...; VPL = 2, 4, 8 or
+// 16, chosen by the autotuner: the kernel is issue bound, and the per-column
+// setup below is paid once per lane for VPL voxels).  Everything that depends only on
 // (i, j) and the view -- the candidate columns within hwu of the voxel
 // column's projection, each column's family, plane m, exact in-plane weight
 // wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
@@ -18,7 +19,10 @@
 // lane's first voxel the offset q_z - k of that row is taken exactly from the
 // Q.40 crossing; the next rows follow by the per-row step, and the next voxel
 // by subtracting one and dropping the rows that fell below its footprint, so
-// wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  The residual arrives transposed and zero-padded
+// wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  A column whose rows
+// are spaced by `step` voxels reaches a voxel with at most
+// floor(2 / step * (1 + 1e-4) + 0.002) + 1 rows; columns that need fewer than
+// the geometry's ntap take a loop one tap shorter (a warp-uniform branch).  The residual arrives transposed and zero-padded
 // (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
 // lanes' row reads are contiguous and need no bounds test.  The gradient is
 // written in z-innermost order [j][i][k], coalesced.
@@ -41,6 +45,32 @@ struct BpArgs {
     double *g2_partials;  // optional: per-block sum of the squared gradient
 };
 
+// The taps of one candidate column for the lane's VPL voxels: window of NT
+// rows from `lo`, whose first crossing lies d0 voxels from the lane's first
+// voxel (-1 < d0 <= -1 + step).
+template <int NT, int VPL>
+__device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
+                                            int lo, float d0, float step, int lo_max) {
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+        // a window clamped into the zero pads holds no real row (ntap <= RT_PAD)
+        const float *r = rcol + min(max(lo, -RT_PAD), lo_max);
+        float sz = 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const float d = fmaf((float)t, step, d0);
+            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(r + t), sz);
+        }
+        acc[q] = fmaf(wb, sz, acc[q]);
+        // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
+        d0 -= 1.f;
+        while (d0 <= -1.f) {
+            ++lo;
+            d0 += step;
+        }
+    }
+}
+
 template <int NTAP, int K2_VPL>
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
     constexpr int K2_KSPAN = K2_LANES * K2_VPL;
@@ -48,7 +78,7 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
     const int lane = threadIdx.x;
     const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
     const int j = blockIdx.y;
-    const int kfirst = blockIdx.z * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+3
+    const int kfirst = blockIdx.z * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+VPL-1
     float acc[K2_VPL];
 #pragma unroll
     for (int q = 0; q < K2_VPL; ++q) acc[q] = 0.f;
@@ -82,7 +112,7 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
             const long long Z = cF.h0 + (long long)m * cF.h1;
             const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;
             const float step = (float)(int)(Z >> 15) * kInv24;  // dq_z per row = 2Z (32-bit path)
-            const float inv = 1.f / step;                       // rows per voxel
+            const float inv = __fdividef(1.f, step);            // rows per voxel (estimate)
             const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * step;
             // first row whose crossing lies above kfirst - 1: estimate, then one exact correction
             int lo = (int)ceilf(((float)kfirst - zoff_f) * inv - inv);
@@ -96,24 +126,10 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
                 d0 -= step;
             }
             const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
-#pragma unroll
-            for (int q = 0; q < K2_VPL; ++q) {
-                // a window clamped into the zero pads holds no real row (ntap <= RT_PAD)
-                const float *r = rcol + min(max(lo, -RT_PAD), lo_max);
-                float sz = 0.f;
-#pragma unroll
-                for (int t = 0; t < NTAP; ++t) {
-                    const float d = fmaf((float)t, step, d0);
-                    sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(r + t), sz);
-                }
-                acc[q] = fmaf(wb, sz, acc[q]);
-                // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
-                d0 -= 1.f;
-                while (d0 <= -1.f) {
-                    ++lo;
-                    d0 += step;
-                }
-            }
+            if (NTAP > 1 && (int)(2.f * inv * 1.0001f + 0.002f) + 1 < NTAP)
+                column_taps<(NTAP > 1 ? NTAP - 1 : 1), K2_VPL>(acc, wb, rcol, lo, d0, step, lo_max);
+            else
+                column_taps<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, lo_max);
         }
     }
     float g2 = 0.f;
@@ -140,9 +156,23 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
 
 }  // namespace
 
+static int k2_vpl_of(const DevGeom &g) {
+    return (g.k2_vpl == 2 || g.k2_vpl == 8 || g.k2_vpl == 16) ? g.k2_vpl : 4;
+}
+
 int backproject_num_partials(const DevGeom &g) {
-    const int vpl = g.k2_vpl == 2 ? 2 : 4;
+    const int vpl = k2_vpl_of(g);
     return ((g.nx + K2_WARPS - 1) / K2_WARPS) * g.ny * ((g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
+}
+
+template <int NT>
+static void launch_k2(int vpl, dim3 grid, dim3 block, cudaStream_t st, const BpArgs &a) {
+    switch (vpl) {
+        case 2: k2_backproject<NT, 2><<<grid, block, 0, st>>>(a); break;
+        case 8: k2_backproject<NT, 8><<<grid, block, 0, st>>>(a); break;
+        case 16: k2_backproject<NT, 16><<<grid, block, 0, st>>>(a); break;
+        default: k2_backproject<NT, 4><<<grid, block, 0, st>>>(a); break;
+    }
 }
 
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
@@ -157,27 +187,18 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
     a.scale = scale;
     a.gzi = gzi;
     dim3 block(K2_LANES, K2_WARPS);
-    const int vpl = g.k2_vpl == 2 ? 2 : 4;
+    const int vpl = k2_vpl_of(g);
     dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
-#define FBL_K2_CASE(NT)                                                  \
-    case NT:                                                             \
-        if (vpl == 2) k2_backproject<NT, 2><<<grid, block, 0, st>>>(a); \
-        else k2_backproject<NT, 4><<<grid, block, 0, st>>>(a);          \
-        break;
     switch (g.ntap) {  // rows per voxel and column, fixed per geometry (<= RT_PAD)
-        FBL_K2_CASE(1)
-        FBL_K2_CASE(2)
-        FBL_K2_CASE(3)
-        FBL_K2_CASE(4)
-        FBL_K2_CASE(5)
-        FBL_K2_CASE(6)
-        FBL_K2_CASE(7)
-        default:
-            if (vpl == 2) k2_backproject<8, 2><<<grid, block, 0, st>>>(a);
-            else k2_backproject<8, 4><<<grid, block, 0, st>>>(a);
-            break;
+        case 1: launch_k2<1>(vpl, grid, block, st, a); break;
+        case 2: launch_k2<2>(vpl, grid, block, st, a); break;
+        case 3: launch_k2<3>(vpl, grid, block, st, a); break;
+        case 4: launch_k2<4>(vpl, grid, block, st, a); break;
+        case 5: launch_k2<5>(vpl, grid, block, st, a); break;
+        case 6: launch_k2<6>(vpl, grid, block, st, a); break;
+        case 7: launch_k2<7>(vpl, grid, block, st, a); break;
+        default: launch_k2<8>(vpl, grid, block, st, a); break;
     }
-#undef FBL_K2_CASE
     return cudaGetLastError();
 }
 

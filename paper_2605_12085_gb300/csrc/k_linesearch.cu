@@ -20,19 +20,28 @@ __global__ void k_ls_init(LSState *ls) {
     ls->status = FBL_OK;
 }
 
-// Input features of the step proposal (all scale-free), from this
-// iteration's f_N(x) and ||grad f_N(x)||^2 and the previous accepted one.
+// Input features of the step proposal, from this iteration's f = f_N(x) and
+// g2 = ||grad f_N(x)||^2 and the previous accepted iterations.  With the
+// curvature index c = log2(alpha_0 g2 / (2 f)) (g2 / (2 f) <= L), only relative
+// quantities enter once there is a previous iteration, so that a network
+// trained on small volumes transfers to large ones:
+//   0: c/10 at the first iteration (0 afterwards), 1: log(f / f_prev),
+//   2: log(|g| / |g_prev|), 3: (c - c_prev)/10, 4: N_t / n_theta,
+//   5: log(1 + k)/10, 6: 1 if there is a previous iteration,
+//   7: (j_prev - j_prevprev)/4, the last change of the accepted grid index.
 __device__ void proposal_features(const LSState &ls, const PropState &ps, double f, double g2,
                                   float *feat) {
     const bool have = ps.have_prev != 0;
-    feat[0] = have ? 0.1f * (float)ps.j_prev : 0.f;
+    const double c = log2(fmax(ls.alpha_init * g2 / fmax(2.0 * f, 1e-300), 1e-300));
+    const double c_prev = log2(fmax(ls.alpha_init * ps.g2_prev / fmax(2.0 * ps.f_prev, 1e-300), 1e-300));
+    feat[0] = have ? 0.f : (float)(0.1 * c);
     feat[1] = have ? (float)log(fmax(f, 1e-300) / fmax(ps.f_prev, 1e-300)) : 0.f;
     feat[2] = have ? (float)(0.5 * log(fmax(g2, 1e-300) / fmax(ps.g2_prev, 1e-300))) : 0.f;
-    feat[3] = (float)(0.1 * log2(fmax(ls.alpha_init * g2 / fmax(2.0 * f, 1e-300), 1e-300)));
+    feat[3] = have ? (float)(0.1 * (c - c_prev)) : 0.f;
     feat[4] = (float)ls.N_t / (float)ls.n_theta;
     feat[5] = (float)(0.1 * log(1.0 + (double)ps.k));
     feat[6] = have ? 1.f : 0.f;
-    feat[7] = (float)(0.1 * log10(fmax(f, 1e-300)));
+    feat[7] = ps.have_dj ? 0.25f * (float)ps.dj_prev : 0.f;
 }
 
 // One warp: features, the network (hidden units l and l+32 per lane), the
@@ -70,8 +79,14 @@ __global__ void k_propose(LSState *ls, const PropState *ps, const double *sc, co
         pred = part + params[OB3];
     }
     if (lane == 0) {
+        // the network predicts the change of the grid index from the previous
+        // accepted one; rounding down (margin) prefers one extra trial to a
+        // halved step
         int j = 0;
-        if (params && isfinite(pred)) j = min(max((int)rintf(pred - margin), 0), ls->max_backtracks);
+        if (params && isfinite(pred)) {
+            const float base = ps->have_prev ? (float)ps->j_prev : 0.f;
+            j = min(max((int)floorf(base + pred + 0.5f - margin), 0), ls->max_backtracks);
+        }
         double a = ls->alpha_init;
         for (int q = 0; q < j; ++q) a = __dmul_rn(a, ls->beta);  // the plain rule's step grid
         ls->alpha_init = a;
@@ -105,7 +120,10 @@ __global__ void k_ls_decide(LSState *ls, PropState *ps, const double *sc,
         ls->accepted = 1;
         ps->f_prev = f_x;
         ps->g2_prev = ls->g2;
-        ps->j_prev = ls->j_start + ls->trials;
+        const int j_acc = ls->j_start + ls->trials;
+        ps->dj_prev = j_acc - ps->j_prev;
+        ps->have_dj = ps->have_prev;
+        ps->j_prev = j_acc;
         ps->have_prev = 1;
         ps->k += 1;
     } else if (ls->trials >= ls->max_backtracks) {

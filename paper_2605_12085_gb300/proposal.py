@@ -3,11 +3,14 @@
 The plain method (Step 2d: every line search starts from alpha_0) is run on
 seeded synthetic phantoms; each iteration gives one trace: the proposal's
 eight input features (computed by the solver, fbl_step_stats.features) and
-the number of step reductions the plain rule needed.  The network
-(8 -> 64 -> 64 -> 1, tanh) is fitted to that count with the library's own
-CUDA training kernels (mlp_train), and the solver then starts each search at
-alpha_0 * beta^round(prediction - margin), a point of the plain rule's own
-grid; acceptance (2.3) and backtracking are unchanged.
+the grid index j = log_beta(alpha / alpha_0) of the step the plain rule
+accepted.  The network (8 -> 64 -> 64 -> 1, tanh) is fitted, with the
+library's own CUDA training kernels (mlp_train), to the change of j from the
+previous iteration (to j itself at a run's first iteration): consecutive
+iterations need similar steps, so the change transfers across problem sizes
+where j does not.  The solver then starts each search at
+alpha_0 * beta^floor(j_prev + prediction + 1/2 - margin), a point of the plain
+rule's own grid; acceptance (2.3) and backtracking are unchanged.
 
     python -m paper_2605_12085_gb300.proposal --out PATH [--traces N]
 
@@ -77,7 +80,8 @@ def make_problem(fbl, prob, device):
 
 def generate_traces(target: int, seed: int = 0, epochs: int = 12, use_graph: int = 1, log=print):
     """Run the plain method on seeded problems until `target` traces exist.
-    Returns X [n][8] (float32), t [n] (float32 backtrack counts), info."""
+    Returns X [n][8] (float32), t [n] (float32 change of the accepted grid
+    index), info."""
     import torch
     import paper_2605_12085_gb300 as fbl
     device = torch.device("cuda")
@@ -93,8 +97,11 @@ def generate_traces(target: int, seed: int = 0, epochs: int = 12, use_graph: int
         S = fbl.fblisa_create(G, p)
         x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
         tr = S.run(x, b, epochs)
-        X.append(np.array([t["features"] for t in tr], dtype=np.float32))
-        T.append(np.array([t["j_start"] + t["backtracks"] for t in tr], dtype=np.float32))
+        feats = np.array([t["features"] for t in tr], dtype=np.float32)
+        j_acc = np.array([t["j_start"] + t["backtracks"] for t in tr], dtype=np.float32)
+        j_prev = np.concatenate([[0.0], j_acc[:-1]])  # one uninterrupted run per problem
+        X.append(feats)
+        T.append((j_acc - j_prev).astype(np.float32))
         info.append(dict(prob, iterations=len(tr),
                          mean_backtracks=float(np.mean([t["backtracks"] for t in tr]))))
         log("problem %d: n=%d views=%d N0=%d mu=%g noise=%g -> %d traces, mean backtracks %.2f "
@@ -165,7 +172,9 @@ def main(argv=None):
     X, t, info = generate_traces(args.traces, seed=args.seed)
     t1 = time.time()
     params, rec = train(X, t, epochs=args.epochs, seed=args.seed)
-    meta = dict(network="8-64-64-1 tanh", target="backtracks of the plain rule (j_accepted)",
+    np.savez(os.path.splitext(args.out)[0] + "_traces.npz", X=X, t=t)
+    meta = dict(network="8-64-64-1 tanh",
+                target="change of the plain rule's accepted grid index from the previous iteration",
                 traces=int(len(t)), problems=info, training=rec,
                 trace_seconds=t1 - t0, train_seconds=time.time() - t1,
                 target_mean=float(t.mean()), target_std=float(t.std()))
