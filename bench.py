@@ -35,8 +35,16 @@ if ROOT not in sys.path:
 
 METRIC = "GUPS fwd+back at 512^3/720 views; FB-LISA time-to-1e-3 rel-err vs plain FP32"
 UNIT = "GUPS"
-OPS_PER_SAMPLE = 14      # FP32 ops of one Joseph sample (K1)
+# FP32 ops of one Joseph sample: 2 coordinate updates, 2 floors, 2 fractions,
+# 3 linear interpolations of 2 ops each, 1 accumulate
+OPS_PER_SAMPLE = 14
 K3_BYTES_PER_VOXEL = 12  # read x and g, write x_bar (FP32)
+# DRAM bytes (read + write) of one trial-objective projection launch of the
+# 512^3 / 768^2 / 40-view FP32 workload, from one ncu capture
+# (profiles/dram_traffic_c3_512.md); valid only for the projector source it
+# was taken on, so it is reported only while k_project.cu has that hash.
+K1_TRAFFIC = {"workload": "c3_512", "bytes_per_launch": 11.000e9,
+              "source_sha256": "f47c3b232c1dec7ea3e776bfcc975171501adb8f0ce17932ba28a14a36aca094"}
 
 
 def parse():
@@ -59,6 +67,53 @@ def parse():
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def k1_traffic(workload):
+    """The captured K1 DRAM traffic per launch, or None when it does not apply
+    (another workload, or the projector source changed since the capture)."""
+    import hashlib
+    if workload != K1_TRAFFIC["workload"]:
+        return None
+    src = os.path.join(ROOT, "paper_2605_12085_gb300", "csrc", "k_project.cu")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return K1_TRAFFIC["bytes_per_launch"] if digest == K1_TRAFFIC["source_sha256"] else None
+
+
+def full_sweep(fbl, G, g, xd, device, reps=2):
+    """GUPS of the plain operators over every view: A x for all n_theta views
+    (N samples per ray) and A^T y for all views (N^3 voxel-views per view),
+    each timed with CUDA events after one warm-up, inputs resident in HBM."""
+    import torch
+    stream = torch.cuda.current_stream(device)
+    views = list(range(g.n_views))
+    y = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
+    gr = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, call in (("forward", lambda: fbl.project(G, xd, views, y=y)),
+                       ("back", lambda: fbl.backproject(G, y, views, x=gr))):
+        call()
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    fwd_units = float(g.n_views) * g.nu * g.nv * g.nx
+    bp_units = float(g.n_views) * g.n_vox
+    del y, gr
+    return {"views": g.n_views, "forward_ms": out["forward_ms"], "back_ms": out["back_ms"],
+            "gups_forward": fwd_units / (out["forward_ms"] * 1e-3) / 1e9,
+            "gups_back": bp_units / (out["back_ms"] * 1e-3) / 1e9,
+            "gups_fwd_back": (fwd_units + bp_units) / ((out["forward_ms"] + out["back_ms"]) * 1e-3) / 1e9,
+            "units": "forward: n_views*nu*nv*N ray samples; back: n_views*N^3 voxel-views"}
 
 
 def load_peaks():
@@ -208,7 +263,7 @@ def active_samples(g, views):
     return total
 
 
-def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
+def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
     """Wall time (sum of CUDA-event step times; objective evaluations off the
     clock) for plain FP32 FB-LISA and for learned proposal + BF16 storage +
     graph capture to reach F(x) <= F* (1 + 1e-3), where F* is the plain
@@ -218,6 +273,7 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
     params, meta = proposal.load()
     stream = torch.cuda.current_stream(device)
     b16 = b.to(torch.bfloat16)
+    xt_d = torch.from_numpy(xt).to(device) if xt is not None else None
 
     def run(fast, max_epochs, target=None):
         p = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
@@ -245,8 +301,8 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
             k += 1
             trials += st["backtracks"] + 1
             if k % check_every == 0 or k == n_iter:
-                F = fbl.evaluate(G, x, b, wl.mu)[0]
-                hist.append((k, elapsed, F))
+                F, _, re = fbl.evaluate(G, x, b, wl.mu, x_true=xt_d)
+                hist.append((k, elapsed, F, re))
                 if target is not None and F <= target:
                     break
         return hist, trials / max(k, 1)
@@ -259,6 +315,8 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, log=None):
     fast_hit = next((h for h in fast if h[2] <= target), None)
     out = {"F_star": F_star, "rel_tol": 1e-3, "epochs_for_F_star": epochs,
            "plain_fp32_s": plain_hit[1], "plain_iterations": plain_hit[0],
+           "plain_rel_error_vs_x_true": plain_hit[3] if xt is not None else None,
+           "fast_rel_error_vs_x_true": (fast_hit[3] if fast_hit and xt is not None else None),
            "plain_trials_per_iteration": plain_trials,
            "fast": "learned proposal + BF16 storage + graph-captured iteration",
            "fast_s": fast_hit[1] if fast_hit else None,
@@ -332,7 +390,8 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"kernel": "k1_project (trial objective, Step 2c)", "bound": "alu",
                 "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": (achieved / alu_peak) if achieved else None,
-                "traffic": None,
+                "traffic": k1_traffic(wl.name),
+                "algorithmic_bytes": g.n_vox * 4 + stats[0]["N_t"] * g.nu * g.nv * 4,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock seen)"
                                % sm_clock,
                 "ops_per_sample": OPS_PER_SAMPLE, "samples_per_launch": samples_per_launch,
@@ -361,6 +420,9 @@ def run_ours(args, rank, world, local_rank):
                            "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},
            "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk,
            "autotune": tune}
+
+    if rank == 0:
+        out["full_sweep"] = full_sweep(fbl, G, g, x, device)
 
     # storage-precision variants (BF16 / FP16 iterates and data, FP32 arithmetic)
     if args.variants:
@@ -395,7 +457,7 @@ def run_ours(args, rank, world, local_rank):
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,
-                                                     args.tto_check)
+                                                     args.tto_check, xt=xt)
 
     # end to end through the same C-ABI call with host (pinned) buffers
     if args.e2e_steps > 0:

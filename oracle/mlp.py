@@ -3,8 +3,9 @@
 The paper has no learned component (it resets the step to alpha_0 at every
 iteration, Step 2d); this is the textbook definition of the perceptron the
 library uses, 8 -> 64 -> 64 -> 1 with tanh hidden units, and of its loss
-1/(2n) sum (y - t)^2, with the gradient by the chain rule.  Pinned by central
-finite differences of the loss (tests/test_oracle_mlp.py).  Parameters are
+1/(2n) sum (y - t)^2, with the gradient by the chain rule, and the Adam update
+the training kernel takes.  Pinned by central finite differences of the loss
+and by Adam's closed form under a constant gradient (tests/test_oracle_mlp.py).  Parameters are
 packed as W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.
 """
 import numpy as np
@@ -72,3 +73,16 @@ def gradient(p, X, t):
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(axis=0)
     return pack(g)
+
+
+def adam_step(p, m, v, g, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1): moment estimates
+    m, v updated with the gradient g, bias-corrected by 1 - beta^step (step
+    counts from 1), then p - lr * m_hat / (sqrt(v_hat) + eps).  Returns the new
+    (p, m, v)."""
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return np.asarray(p, dtype=np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

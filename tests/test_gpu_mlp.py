@@ -48,3 +48,37 @@ def test_training_fits_a_smooth_target():
     y = fbl.mlp_forward(P, Xd).double().cpu().numpy()
     yo, _ = mlp.forward(P.double().cpu().numpy(), X.astype(np.float32).astype(np.float64))
     assert np.max(np.abs(y - yo)) <= 1e-5 * (1 + np.abs(yo).max())
+
+
+def test_two_adam_steps_match_fp64_reference():
+    # full-batch minibatches: each kernel step uses the gradient at the current
+    # parameters, so two steps of the kernel must equal two oracle steps
+    import paper_2605_12085_gb300 as fbl
+    rng = np.random.default_rng(4)
+    n = 512
+    X = rng.standard_normal((n, 8)).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    p0 = mlp.init(9).astype(np.float32).astype(np.float64)
+    lr = 1e-3
+    P = _cuda(p0)
+    tr = fbl.MlpTrainer(P)
+    tr.train(_cuda(X), _cuda(t), batch=n, epochs=2, lr=lr)
+    assert int(tr.step.item()) == 2
+    p_gpu = P.double().cpu().numpy()
+    m = np.zeros_like(p0)
+    v = np.zeros_like(p0)
+    p = p0
+    grads = []
+    for step in (1, 2):
+        g = mlp.gradient(p, X, t)
+        grads.append(g)
+        p, m, v = mlp.adam_step(p, m, v, g, step, lr)
+    # Adam moves a parameter by about lr whatever the size of its gradient, so a
+    # gradient within FP32 rounding of zero may flip its step; compare the
+    # parameters whose gradients are clearly non-zero in both steps
+    scale = np.median(np.abs(grads[0]))
+    keep = (np.abs(grads[0]) > 1e-3 * scale) & (np.abs(grads[1]) > 1e-3 * scale)
+    assert keep.mean() > 0.95
+    d_gpu, d_ref = (p_gpu - p0)[keep], (p - p0)[keep]
+    assert np.linalg.norm(d_gpu - d_ref) <= 1e-3 * np.linalg.norm(d_ref)
+    assert np.max(np.abs(p_gpu - p)) <= 2.5 * lr  # any flipped step stays a step
