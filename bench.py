@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--tto-epochs", type=int, default=10,
                     help="epochs of plain FP32 that define F* (0: skip time-to-objective)")
     ap.add_argument("--tto-check", type=int, default=3, help="iterations between F evaluations")
+    ap.add_argument("--batched", type=int, default=1, help="also time the 16-volume batched launch")
     return ap.parse_args()
 
 
@@ -114,6 +115,82 @@ def full_sweep(fbl, G, g, xd, device, reps=2):
             "gups_back": bp_units / (out["back_ms"] * 1e-3) / 1e9,
             "gups_fwd_back": (fwd_units + bp_units) / ((out["forward_ms"] + out["back_ms"]) * 1e-3) / 1e9,
             "units": "forward: n_views*nu*nv*N ray samples; back: n_views*N^3 voxel-views"}
+
+
+def batched_record(fbl, device, wls, label, proposal=False, steps=5, warmup=3):
+    """Uneven volumes in one batch: one fblisa_batch_step per iteration of all
+    volumes (persistent launches, one graph) against the same iterations run
+    volume after volume by graph-mode single-volume solvers, FP32.  Every
+    geometry is tuned once; the batch takes the largest volume's columns per
+    block and each volume's own plane-loop form and voxels per lane, and the
+    single-volume solvers run on exactly the same configurations."""
+    import torch
+    stream = torch.cuda.current_stream(device)
+    data = [make_data(fbl, wl, device) for wl in wls]
+    Gs = [d[0] for d in data]
+    bs = [d[2] for d in data]
+    big = max(range(len(wls)), key=lambda q: wls[q].geom.n_vox)
+    tunes = [fbl.geometry_autotune(G, fbl.F32, wl.N0) for G, wl in zip(Gs, wls)]
+    cols = tunes[big]["k1_cols"]
+    for G, t in zip(Gs, tunes):
+        fbl.geometry_set_launch(G, cols, t["k1_split"], t["k2_vpl"])
+    net = None
+    if proposal:
+        from paper_2605_12085_gb300 import proposal as prop
+        net, _ = prop.load()
+
+    def params(wl, **kw):
+        return fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches, **kw)
+
+    def timed(step_fn):
+        for _ in range(warmup):
+            step_fn()
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        recs = [step_fn() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / steps, recs
+
+    B = fbl.fblisa_batch_create(Gs, [params(wl) for wl in wls])
+    if net is not None:
+        B.set_proposal(net)
+    xs = [torch.zeros(wl.geom.vol_shape, dtype=torch.float32, device=device) for wl in wls]
+    launches0 = B.info()["launches"]
+    b_ms, b_recs = timed(lambda: B.step(xs, bs))
+    b_launches = (B.info()["launches"] - launches0) / (warmup + steps)
+    units = sum(step_units(st, wl.geom) for rec in b_recs for st, wl in zip(rec, wls)) / steps
+    del B, xs
+    Ss = [fbl.fblisa_create(G, params(wl, use_graph=1)) for G, wl in zip(Gs, wls)]
+    if net is not None:
+        for S in Ss:
+            S.set_proposal(net)
+    xs = [torch.zeros(wl.geom.vol_shape, dtype=torch.float32, device=device) for wl in wls]
+    s_ms, s_recs = timed(lambda: [S.step(x, b) for S, x, b in zip(Ss, xs, bs)])
+    s_units = sum(step_units(st, wl.geom) for rec in s_recs for st, wl in zip(rec, wls)) / steps
+    del Ss, xs, data, Gs, bs
+    return {"workload": label, "step_rule": "learned proposal" if proposal else "plain (alpha_0 reset)",
+            "batched_ms_per_iteration": b_ms, "batched_gups": units / (b_ms * 1e-3) / 1e9,
+            "batched_launches_per_iteration": b_launches,
+            "sequential_ms_per_iteration": s_ms, "sequential_gups": s_units / (s_ms * 1e-3) / 1e9,
+            "speedup": s_ms / b_ms, "steps": steps, "warmup": warmup,
+            "launch_config": {"k1_cols": cols, "k1_split": [t["k1_split"] for t in tunes],
+                              "k2_vpl": [t["k2_vpl"] for t in tunes]},
+            "backtracks_per_volume_iteration":
+                statistics.mean(st["backtracks"] for rec in b_recs for st in rec)}
+
+
+def batched_records(fbl, device):
+    import synth
+    c5a = ("c5a: 16 volumes N_i = round(96 + 224 i/15) (96^3..320^3), 120 + 24 i views, "
+           "detector ceil(1.5 N_i)^2, N_0 = ceil(views/12)")
+    small = ("c5s: 16 volumes N_i = round(24 + 56 i/15) (24^3..80^3), 30 + 6 i views, "
+             "detector ceil(1.5 N_i)^2, N_0 = ceil(views/12)")
+    return {"c5a_plain": batched_record(fbl, device, synth.batched_workloads(), c5a),
+            "c5a_learned": batched_record(fbl, device, synth.batched_workloads(), c5a, proposal=True),
+            "c5s_plain": batched_record(fbl, device, synth.batched_small_workloads(), small)}
 
 
 def load_peaks():
@@ -454,6 +531,9 @@ def run_ours(args, rank, world, local_rank):
                               "backtracks_per_step": statistics.mean(st["backtracks"] for st in stv)}
             del Sv, xv, bv
         out["variants"] = variants
+
+    if args.batched and rank == 0:
+        out["batched"] = batched_records(fbl, device)
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,

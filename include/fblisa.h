@@ -337,6 +337,60 @@ FBL_API fbl_status fblisa_profile(fbl_solver *s, int32_t enable, fbl_profile *ou
 /* The views of the most recent iteration's mini-batch N_k (host copy). */
 FBL_API fbl_status fblisa_last_batch(const fbl_solver *s, int32_t *views, int32_t cap, int32_t *n);
 
+/*
+ * Batched FB-LISA over several independent volumes (no counterpart in the
+ * paper, which reconstructs one volume): each volume v runs its own
+ * Algorithm 1 -- geometry geoms[v], parameters params[v] (its own N_0,
+ * schedule, seed, mu, ...), line search (2.3) and step proposal -- and one
+ * call of fblisa_batch_step advances every volume by one iteration.  On the
+ * GPU each phase of that iteration (residual projection, gradient, and, per
+ * trial, prox + trial objective + decision) is ONE persistent launch over the
+ * tiles of all volumes, and the whole iteration including every volume's
+ * backtracking is one CUDA graph (a WHILE node that repeats while any volume
+ * is still searching).  A volume's iterates are bit-identical to those of a
+ * single-volume solver with the same geometry, parameters and launch
+ * configuration.
+ *
+ * fblisa_batch_create -- n_vol in [1, 1024]; every geometry on one device;
+ *   all params[v] with the same x_dtype and b_dtype, and b_dtype == x_dtype
+ *   (FBL_E_UNSUPPORTED otherwise).  Launch configuration: the projector's
+ *   columns per block (k1_cols) is the largest volume's, for all; every
+ *   volume keeps its own geometry's plane-loop form (k1_split) and voxels per
+ *   lane (k2_vpl), as set by geometry_autotune / geometry_set_launch.
+ *   params[v].autotune and use_graph are ignored.  Copies what it needs; the
+ *   geometries must outlive the batch.
+ * fblisa_batch_set_proposal -- one network (FBL_MLP_PARAMS floats, host or
+ *   device, copied) and margin for every volume, as fblisa_set_proposal;
+ *   enable switches the proposal on or off for every volume.
+ * fblisa_batch_step -- x[v]: [nz][ny][nx] of x_dtype, in and out (device or
+ *   host); b[v]: the full sinogram [n_views][nv][nu] of b_dtype (device or
+ *   host); stats: n_vol records or NULL.  Returns FBL_OK when every volume
+ *   accepted a step; otherwise the status of the first volume that did not
+ *   (FBL_E_LINESEARCH / FBL_E_NONFINITE, also in its stats record): that
+ *   volume's x and schedule position are unchanged, the others advanced.
+ * fblisa_batch_run -- `iterations` batched steps with x loaded and stored
+ *   once; trace (nullable): trace_cap rows of n_vol records; *n_steps = steps
+ *   completed (a failing step stops the run).
+ * fblisa_batch_info -- launch_cfg[4] = {k1_cols, k1_split and k2_vpl of the
+ *   largest volume, the batch's tap count} (nullable); *launches = kernels
+ *   launched by its iterations so far.
+ * fblisa_batch_last_batch -- fblisa_last_batch of volume v.
+ */
+typedef struct fbl_batch fbl_batch;  /* opaque, library-owned */
+FBL_API fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, const fbl_params *params,
+                                       int32_t n_vol, fbl_batch **out);
+FBL_API void fblisa_batch_destroy(fbl_batch *bt);
+FBL_API fbl_status fblisa_batch_set_proposal(fbl_batch *bt, const float *params, float margin,
+                                             int32_t enable);
+FBL_API fbl_status fblisa_batch_step(fbl_batch *bt, void *const *x, const void *const *b,
+                                     fbl_step_stats *stats, void *stream);
+FBL_API fbl_status fblisa_batch_run(fbl_batch *bt, void *const *x, const void *const *b,
+                                    int32_t iterations, fbl_step_stats *trace, int64_t trace_cap,
+                                    int64_t *n_steps, void *stream);
+FBL_API fbl_status fblisa_batch_info(const fbl_batch *bt, int32_t *launch_cfg, int64_t *launches);
+FBL_API fbl_status fblisa_batch_last_batch(const fbl_batch *bt, int32_t v, int32_t *views, int32_t cap,
+                                           int32_t *n);
+
 /* Message of the last failed call on this thread ("" if none). */
 FBL_API const char *fbl_last_error(void);
 

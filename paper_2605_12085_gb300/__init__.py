@@ -81,7 +81,9 @@ EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_
            "fblisa_run", "fblisa_last_batch", "fbl_last_error", "fbl_schedule",
            "fbl_epoch_batches", "prox_reduce_static", "geometry_autotune",
            "geometry_set_launch", "evaluate", "mlp_forward", "mlp_gradient", "mlp_train",
-           "fblisa_set_proposal"]
+           "fblisa_set_proposal", "fblisa_batch_create", "fblisa_batch_destroy",
+           "fblisa_batch_set_proposal", "fblisa_batch_step", "fblisa_batch_run",
+           "fblisa_batch_info", "fblisa_batch_last_batch"]
 
 
 def _load():
@@ -113,6 +115,13 @@ def _load():
         "fblisa_last_batch": (st, [vp, P(i32), i32, P(i32)]),
         "fblisa_profile": (st, [vp, i32, P(fbl_profile)]),
         "fblisa_set_proposal": (st, [vp, vp, ctypes.c_float, i32]),
+        "fblisa_batch_create": (st, [P(vp), P(fbl_params), i32, P(vp)]),
+        "fblisa_batch_destroy": (None, [vp]),
+        "fblisa_batch_set_proposal": (st, [vp, vp, ctypes.c_float, i32]),
+        "fblisa_batch_step": (st, [vp, P(vp), P(vp), P(fbl_step_stats), vp]),
+        "fblisa_batch_run": (st, [vp, P(vp), P(vp), i32, P(fbl_step_stats), i64, P(i64), vp]),
+        "fblisa_batch_info": (st, [vp, P(i32), P(i64)]),
+        "fblisa_batch_last_batch": (st, [vp, i32, P(i32), i32, P(i32)]),
         "fbl_last_error": (ctypes.c_char_p, []),
         "fbl_schedule": (st, [i32, i32, i32, dbl, dbl, i32, P(i32), P(i32)]),
         "fbl_epoch_batches": (st, [ctypes.c_uint64, i32, i32, i32, P(i32)]),
@@ -421,6 +430,79 @@ class Solver:
 
 def fblisa_create(geom: Geometry, params: fbl_params) -> Solver:
     return Solver(geom, params)
+
+
+class Batch:
+    """Handle of a fbl_batch: one Algorithm 1 per volume, every phase of an
+    iteration of all volumes in one persistent launch (fblisa_batch_*)."""
+
+    def __init__(self, geoms: Sequence[Geometry], params: Sequence[fbl_params]):
+        if len(geoms) != len(params) or not geoms:
+            raise ValueError("one parameter record per geometry")
+        self.geoms = list(geoms)  # keep the geometries alive
+        self.n = len(geoms)
+        gh = (ctypes.c_void_p * self.n)(*[g.handle.value for g in geoms])
+        pa = (fbl_params * self.n)(*params)
+        h = ctypes.c_void_p()
+        _check(lib.fblisa_batch_create(gh, pa, self.n, ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fblisa_batch_destroy(h)
+            self.handle = None
+
+    def _arrays(self, xs, bs):
+        if len(xs) != self.n or len(bs) != self.n:
+            raise ValueError("one x and one b per volume")
+        xp = (ctypes.c_void_p * self.n)(*[_ptr(x) for x in xs])
+        bp = (ctypes.c_void_p * self.n)(*[_ptr(b) for b in bs])
+        return xp, bp
+
+    def set_proposal(self, params, margin: float = 0.25, enable: bool = True):
+        _check(lib.fblisa_batch_set_proposal(self.handle, None if params is None else _ptr(params),
+                                             float(margin), int(bool(enable))))
+
+    def step_raw(self, xs, bs, stream=None):
+        """One iteration of every volume: (status, [stats per volume])."""
+        xp, bp = self._arrays(xs, bs)
+        st = (fbl_step_stats * self.n)()
+        rc = lib.fblisa_batch_step(self.handle, xp, bp, st, _stream(*xs, *bs, stream=stream))
+        return rc, [st[v].as_dict() for v in range(self.n)]
+
+    def step(self, xs, bs, stream=None):
+        rc, st = self.step_raw(xs, bs, stream=stream)
+        _check(rc)
+        return st
+
+    def run(self, xs, bs, iterations: int, stream=None):
+        """`iterations` batched steps; returns [[stats per volume] per step]."""
+        xp, bp = self._arrays(xs, bs)
+        cap = max(1, iterations)
+        trace = (fbl_step_stats * (cap * self.n))()
+        n = ctypes.c_int64()
+        _check(lib.fblisa_batch_run(self.handle, xp, bp, int(iterations), trace, cap, ctypes.byref(n),
+                                    _stream(*xs, *bs, stream=stream)))
+        return [[trace[q * self.n + v].as_dict() for v in range(self.n)] for q in range(n.value)]
+
+    def info(self):
+        cfg = (ctypes.c_int32 * 4)()
+        n = ctypes.c_int64()
+        _check(lib.fblisa_batch_info(self.handle, cfg, ctypes.byref(n)))
+        return {"k1_cols": cfg[0], "k1_split": cfg[1], "k2_vpl": cfg[2], "ntap": cfg[3],
+                "launches": n.value}
+
+    def last_batch(self, v: int):
+        n = ctypes.c_int32()
+        _check(lib.fblisa_batch_last_batch(self.handle, v, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int32 * max(1, n.value))()
+        _check(lib.fblisa_batch_last_batch(self.handle, v, buf, n.value, ctypes.byref(n)))
+        return list(buf[:n.value])
+
+
+def fblisa_batch_create(geoms, params) -> Batch:
+    return Batch(geoms, params)
 
 
 def fbl_schedule(n_theta, N0, n_max, C, eps_base, epochs):

@@ -1556,3 +1556,523 @@ extern "C" fbl_status fblisa_last_batch(const fbl_solver *s, int32_t *views, int
 extern "C" const char *fbl_last_error(void) { return g_last_error.c_str(); }
 
 void fbl::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+// ---------------------------------------------------------------------------
+// Batched iteration over several volumes: every volume runs its own
+// Algorithm 1 (geometry, schedule, sampling, line search), and each phase of
+// one iteration of all of them is one persistent launch (fbl_internal.cuh).
+
+struct fbl_batch {
+    int device = -1;
+    int n_vol = 0;
+    std::vector<fbl_solver *> sv;   // per-volume state and buffers
+    std::vector<int> order;         // volumes in tile order (largest first)
+    int x_dtype = FBL_F32, b_dtype = FBL_F32;
+    int cols = 8, split = 1, vpl = 4, ntap = 1;
+    // descriptor blob: BatchHdr, BatchVol[n_vol] (tile order), view lists
+    size_t blob_bytes = 0, vols_off = 0, views_off = 0;
+    std::vector<size_t> view_slot;  // offset (in int32) of each volume's view list
+    void *d_blob = nullptr, *h_blob = nullptr;
+    LSState *d_ls = nullptr, *h_ls = nullptr;  // [n_vol], volume order
+    int *d_ctr = nullptr;                      // 2 ints per persistent launch site
+    float *d_mlp = nullptr;
+    bool have_mlp = false;
+    float margin = 0.25f;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    int64_t k = 0;
+    int64_t launches = 0;                      // kernels launched by the batch so far
+};
+
+namespace {
+
+constexpr int BATCH_SITES = 4;  // persistent launch sites: K1 residual, K2, K3, K1 objective
+
+void batch_free(fbl_batch *bt) {
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+    if (bt->cap2) cudaStreamDestroy(bt->cap2);
+    cudaFree(bt->d_blob);
+    cudaFreeHost(bt->h_blob);
+    cudaFree(bt->d_ls);
+    cudaFreeHost(bt->h_ls);
+    cudaFree(bt->d_ctr);
+    cudaFree(bt->d_mlp);
+    for (fbl_solver *s : bt->sv) {
+        if (!s) continue;
+        solver_free(s);
+        delete s;
+    }
+    bt->sv.clear();
+}
+
+BatchHdr *blob_hdr(fbl_batch *bt, bool dev) {
+    return (BatchHdr *)((char *)(dev ? bt->d_blob : bt->h_blob));
+}
+BatchVol *blob_vols(fbl_batch *bt, bool dev) {
+    return (BatchVol *)((char *)(dev ? bt->d_blob : bt->h_blob) + bt->vols_off);
+}
+int32_t *blob_views(fbl_batch *bt, bool dev) {
+    return (int32_t *)((char *)(dev ? bt->d_blob : bt->h_blob) + bt->views_off);
+}
+
+// The whole batched iteration (Steps 2b-2c of every volume) as one graph.
+fbl_status batch_build_graph(fbl_batch *bt) {
+    if (!bt->cap) CK(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking), "capture stream");
+    if (!bt->cap2) CK(cudaStreamCreateWithFlags(&bt->cap2, cudaStreamNonBlocking), "capture stream");
+    const BatchHdr *hdr = blob_hdr(bt, true);
+    BatchVol *vols = blob_vols(bt, true);
+    const int n = bt->n_vol;
+    cudaStream_t cs = bt->cap, cb = bt->cap2;
+    // relaxed: the persistent launchers query occupancy on first use
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed), "begin capture");
+    cudaError_t e = launch_batch_project(PROJ_RESID, hdr, vols, bt->x_dtype, bt->b_dtype, bt->cols,
+                                         bt->d_ctr + 0, cs);
+    if (e == cudaSuccess) e = launch_batch_reduce(hdr, vols, n, 0, 1, 0, 0, cs);
+    if (e == cudaSuccess) e = launch_batch_backproject(hdr, vols, bt->ntap, bt->d_ctr + 2, cs);
+    if (e == cudaSuccess) e = launch_batch_reduce(hdr, vols, n, 1, 1, 5, 0, cs);
+    if (e == cudaSuccess) e = launch_batch_propose(vols, n, bt->have_mlp ? bt->d_mlp : nullptr, bt->margin, cs);
+    if (e == cudaSuccess) e = launch_batch_ls_init(blob_hdr(bt, true), vols, n, cs);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaError_t eb = launch_batch_prox(hdr, vols, bt->x_dtype, bt->d_ctr + 4, cb);
+            if (eb == cudaSuccess) eb = launch_batch_reduce(hdr, vols, n, 2, 3, 1, 1, cb);
+            if (eb == cudaSuccess)
+                eb = launch_batch_project(PROJ_NORM, hdr, vols, bt->x_dtype, bt->b_dtype, bt->cols,
+                                          bt->d_ctr + 6, cb);
+            if (eb == cudaSuccess) eb = launch_batch_reduce(hdr, vols, n, 0, 1, 4, 1, cb);
+            if (eb == cudaSuccess) eb = launch_batch_decide(blob_hdr(bt, true), vols, n, cond, cb);
+            cudaError_t ee = cudaStreamEndCapture(cb, &body);
+            e = eb != cudaSuccess ? eb : ee;
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->h_ls, bt->d_ls, (size_t)n * sizeof(LSState), cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        bt->exec = nullptr;
+        return cuda_fail(e, "graph capture of the batched iteration");
+    }
+    return FBL_OK;
+}
+
+// One iteration of every volume.  stats: [n_vol] (volume order), may be NULL.
+// Returns FBL_OK when every volume accepted a step; otherwise the status of
+// the first volume that did not (its x and schedule position are unchanged;
+// the other volumes have advanced).
+fbl_status batch_iterate(fbl_batch *bt, const void *const *b, const char *b_dev, fbl_step_stats *stats,
+                         cudaStream_t st) {
+    const int n = bt->n_vol;
+    struct Saved {
+        int32_t epoch, N_t, N_prev, iters, it;
+        int64_t khat;
+        bool new_epoch;
+        std::vector<int32_t> views;
+    };
+    std::vector<Saved> saved(n);
+    auto restore = [&](int v) {
+        fbl_solver *s = bt->sv[v];
+        const Saved &sv = saved[v];
+        s->epoch = sv.epoch;
+        s->N_t = sv.N_t;
+        s->N_prev = sv.N_prev;
+        s->iters_epoch = sv.iters;
+        s->iter_in_epoch = sv.it;
+        s->k_hat = sv.khat;
+        if (sv.new_epoch) s->epoch_views = sv.views;
+    };
+    BatchHdr *hh = blob_hdr(bt, false);
+    BatchVol *hv = blob_vols(bt, false);
+    int32_t *hviews = blob_views(bt, false);
+    const int32_t *dviews = blob_views(bt, true);
+    hh->n_vol = n;
+    int first[3] = {0, 0, 0};
+    for (int q = 0; q < n; ++q) {
+        const int v = bt->order[q];
+        fbl_solver *s = bt->sv[v];
+        const fbl_geometry_desc &d = s->g->desc;
+        Saved &sv = saved[v];
+        sv.epoch = s->epoch;
+        sv.N_t = s->N_t;
+        sv.N_prev = s->N_prev;
+        sv.iters = s->iters_epoch;
+        sv.it = s->iter_in_epoch;
+        sv.khat = s->k_hat;
+        sv.new_epoch = !(s->epoch > 0 && s->iter_in_epoch < s->iters_epoch);
+        if (sv.new_epoch) sv.views = s->epoch_views;
+        begin_epoch_if_needed(s);
+        const int32_t N = s->N_t;
+        fbl_status rc = ensure_batch_buffers(s, N);
+        if (rc) {
+            for (int r = 0; r <= q; ++r) restore(bt->order[r]);
+            return rc;
+        }
+        const int32_t *views = s->epoch_views.data() + (size_t)s->iter_in_epoch * N;
+        std::memcpy(hviews + bt->view_slot[v], views, N * sizeof(int32_t));
+        s->last_batch.assign(views, views + N);
+        const void *bd = b[v];
+        const int32_t *bmap = dviews + bt->view_slot[v];
+        if (!b_dev[v]) {  // stage the batch's views of host data
+            const size_t per_view = (size_t)d.nv * d.nu * dtype_size(s->p.b_dtype);
+            if (per_view * N > s->bstage_cap) {
+                cudaFree(s->bstage);
+                s->bstage = nullptr;
+                s->bstage_cap = 0;
+                cudaError_t e = cudaMalloc(&s->bstage, per_view * N);
+                if (e != cudaSuccess) {
+                    for (int r = 0; r <= q; ++r) restore(bt->order[r]);
+                    return cuda_fail(e, "data staging");
+                }
+                s->bstage_cap = per_view * N;
+            }
+            for (int32_t w = 0; w < N; ++w)
+                CK(cudaMemcpyAsync((char *)s->bstage + per_view * w, (const char *)b[v] + per_view * views[w],
+                                   per_view, cudaMemcpyHostToDevice, st),
+                   "data H2D");
+            bd = s->bstage;
+            bmap = nullptr;
+        }
+        BatchVol &bv = hv[q];
+        std::memset(&bv, 0, sizeof bv);
+        bv.g = s->dg;
+        bv.L = s->L;
+        bv.x_cur = s->st;
+        bv.x_trial = s->tr;
+        bv.b = bd;
+        bv.b_views = bmap;
+        bv.views = dviews + bt->view_slot[v];
+        bv.rt = s->rt;
+        bv.grad = s->grad;
+        bv.partials = s->partials;
+        bv.sc = s->d_sc;
+        bv.ls = bt->d_ls + v;
+        bv.ps = s->d_ps;
+        bv.scale = (float)((double)d.n_views / (double)N);
+        bv.N_t = N;
+        bv.proposal = s->p.proposal;
+        bv.tiles[0] = project_num_partials(s->dg, N);
+        bv.tiles[1] = backproject_num_partials(s->dg);
+        bv.tiles[2] = prox_zi_num_partials(d.nx, d.ny, d.nz);
+        for (int ph = 0; ph < 3; ++ph) {
+            bv.first[ph] = first[ph];
+            first[ph] += bv.tiles[ph];
+        }
+        LSState &cfg = bt->h_ls[v];
+        std::memset(&cfg, 0, sizeof cfg);
+        cfg.alpha_init = s->p.alpha0;
+        cfg.beta = s->p.beta;
+        cfg.mu = s->p.mu;
+        cfg.scale = (double)d.n_views / (double)N;
+        cfg.max_backtracks = s->p.max_backtracks;
+        cfg.force_reject = s->p.force_reject;
+        cfg.N_t = N;
+        cfg.n_theta = d.n_views;
+    }
+    for (int ph = 0; ph < 3; ++ph) hh->total[ph] = first[ph];
+    auto fail_all = [&](fbl_status r) {
+        for (int v = 0; v < n; ++v) restore(v);
+        return r;
+    };
+    cudaError_t e = cudaMemcpyAsync(bt->d_blob, bt->h_blob, bt->blob_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->d_ls, bt->h_ls, (size_t)n * sizeof(LSState), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_all(cuda_fail(e, "batch descriptors"));
+    if (!bt->exec) {
+        fbl_status rc = batch_build_graph(bt);
+        if (rc) return fail_all(rc);
+    }
+    e = cudaGraphLaunch(bt->exec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_all(cuda_fail(e, "batched iteration"));
+    int max_trials = 0;
+    fbl_status first_bad = FBL_OK;
+    int bad_v = -1;
+    for (int v = 0; v < n; ++v) {
+        fbl_solver *s = bt->sv[v];
+        const LSState r = bt->h_ls[v];
+        max_trials = std::max(max_trials, r.trials + 1);
+        const bool accepted = r.status == FBL_OK && r.accepted;
+        if (stats) {
+            fbl_step_stats &o = stats[v];
+            std::memset(&o, 0, sizeof o);
+            o.k = s->k;
+            o.epoch = s->epoch;
+            o.N_t = s->N_t;
+            o.backtracks = r.trials;
+            o.alpha = r.alpha;
+            o.alpha_init = r.alpha_init;
+            o.j_start = r.j_start;
+            o.pred = r.pred;
+            o.grad_norm2 = r.g2;
+            for (int q = 0; q < MLP_IN; ++q) o.features[q] = r.feat[q];
+            o.rho0 = r.rho0;
+            o.f_x = r.f_x;
+            o.f_xbar = r.f_xbar;
+            o.gTd = r.gTd;
+            o.dnorm2 = r.dd;
+            o.margin = r.rhs - r.f_xbar;
+            o.status = accepted ? FBL_OK : (r.status ? r.status : FBL_E_LINESEARCH);
+        }
+        if (accepted) {
+            std::swap(s->st, s->tr);  // mirrors the swap the decision kernel made
+            s->k += 1;
+            s->iter_in_epoch += 1;
+        } else {
+            restore(v);
+            if (first_bad == FBL_OK) {
+                first_bad = r.status == FBL_E_NONFINITE ? FBL_E_NONFINITE : FBL_E_LINESEARCH;
+                bad_v = v;
+            }
+        }
+    }
+    bt->k += 1;
+    bt->launches += 6 + 5 * (int64_t)max_trials;
+    if (first_bad != FBL_OK) {
+        if (first_bad == FBL_E_NONFINITE)
+            return fail(FBL_E_NONFINITE, "fblisa_batch_step: volume %d: non-finite objective or reduction", bad_v);
+        return fail(FBL_E_LINESEARCH, "fblisa_batch_step: volume %d: no step passed (2.3) within the cap", bad_v);
+    }
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, const fbl_params *params,
+                                          int32_t n_vol, fbl_batch **out) {
+    if (!geoms || !params || !out) return fail(FBL_E_INVAL, "fblisa_batch_create: null argument");
+    *out = nullptr;
+    if (n_vol < 1 || n_vol > 1024) return fail(FBL_E_INVAL, "fblisa_batch_create: need 1 <= n_vol <= 1024");
+    for (int v = 0; v < n_vol; ++v)
+        if (!geoms[v]) return fail(FBL_E_INVAL, "fblisa_batch_create: null geometry %d", v);
+    const int dev = geoms[0]->device;
+    for (int v = 0; v < n_vol; ++v) {
+        if (geoms[v]->device != dev) return fail(FBL_E_INVAL, "fblisa_batch_create: geometries on different devices");
+        if (params[v].x_dtype != params[0].x_dtype || params[v].b_dtype != params[0].b_dtype)
+            return fail(FBL_E_INVAL, "fblisa_batch_create: every volume needs the same x_dtype and b_dtype");
+    }
+    if (params[0].b_dtype != params[0].x_dtype)
+        return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: b_dtype must equal x_dtype");
+    fbl_status st = check_device(dev);
+    if (st) return st;
+    auto bt = new fbl_batch();
+    bt->device = dev;
+    bt->n_vol = n_vol;
+    bt->x_dtype = params[0].x_dtype;
+    bt->b_dtype = params[0].b_dtype;
+    // launch configuration shared by the batch: the largest volume's
+    int big = 0;
+    for (int v = 1; v < n_vol; ++v) {
+        const fbl_geometry_desc &a = geoms[v]->desc, &c = geoms[big]->desc;
+        if ((int64_t)a.nx * a.ny * a.nz > (int64_t)c.nx * c.ny * c.nz) big = v;
+    }
+    bt->cols = geoms[big]->dg.k1_cols == 4 ? 4 : 8;
+    bt->split = geoms[big]->dg.k1_split ? 1 : 0;
+    bt->vpl = geoms[big]->dg.k2_vpl;
+    bt->ntap = 1;
+    for (int v = 0; v < n_vol; ++v) bt->ntap = std::max(bt->ntap, geoms[v]->dg.ntap);
+    bt->sv.assign(n_vol, nullptr);
+    for (int v = 0; v < n_vol; ++v) {
+        fbl_params p = params[v];
+        p.autotune = 0;
+        p.use_graph = 0;
+        fbl_solver *s = nullptr;
+        st = fblisa_create(geoms[v], &p, &s);
+        if (st) {
+            std::string keep = g_last_error;
+            batch_free(bt);
+            delete bt;
+            g_last_error = "fblisa_batch_create: volume " + std::to_string(v) + ": " + keep;
+            return st;
+        }
+        s->dg.k1_cols = bt->cols;  // the block width is common; split and vpl stay per volume
+        bt->sv[v] = s;
+    }
+    bt->order.resize(n_vol);
+    for (int v = 0; v < n_vol; ++v) bt->order[v] = v;
+    std::stable_sort(bt->order.begin(), bt->order.end(), [&](int a, int c) {
+        const fbl_geometry_desc &da = geoms[a]->desc, &dc = geoms[c]->desc;
+        return (int64_t)da.nx * da.ny * da.nz > (int64_t)dc.nx * dc.ny * dc.nz;
+    });
+    bt->vols_off = (sizeof(BatchHdr) + 255) / 256 * 256;
+    bt->views_off = bt->vols_off + ((size_t)n_vol * sizeof(BatchVol) + 255) / 256 * 256;
+    bt->view_slot.resize(n_vol);
+    size_t nviews = 0;
+    for (int v = 0; v < n_vol; ++v) {
+        bt->view_slot[v] = nviews;
+        nviews += (size_t)geoms[v]->desc.n_views;
+    }
+    bt->blob_bytes = bt->views_off + nviews * sizeof(int32_t);
+    cudaError_t e = cudaMalloc(&bt->d_blob, bt->blob_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_blob, bt->blob_bytes);
+    if (e == cudaSuccess) std::memset(bt->h_blob, 0, bt->blob_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_ls, (size_t)n_vol * sizeof(LSState));
+    if (e == cudaSuccess) e = cudaMallocHost(&bt->h_ls, (size_t)n_vol * sizeof(LSState));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_ctr, 2 * BATCH_SITES * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(bt->d_ctr, 0, 2 * BATCH_SITES * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_mlp, MLP_PARAMS * sizeof(float));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        batch_free(bt);
+        delete bt;
+        return cuda_fail(e, "fblisa_batch_create");
+    }
+    *out = bt;
+    return FBL_OK;
+}
+
+extern "C" void fblisa_batch_destroy(fbl_batch *bt) {
+    if (!bt) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != bt->device) cudaSetDevice(bt->device);
+    cudaDeviceSynchronize();
+    batch_free(bt);
+    if (cur >= 0 && cur != bt->device) cudaSetDevice(cur);
+    delete bt;
+}
+
+extern "C" fbl_status fblisa_batch_set_proposal(fbl_batch *bt, const float *params, float margin,
+                                                int32_t enable) {
+    if (!bt || (enable && !params && !bt->have_mlp))
+        return fail(FBL_E_INVAL, "fblisa_batch_set_proposal: null argument");
+    if (!std::isfinite(margin)) return fail(FBL_E_INVAL, "fblisa_batch_set_proposal: bad margin");
+    fbl_status st = check_device(bt->device);
+    if (st) return st;
+    if (params) {
+        CK(cudaMemcpy(bt->d_mlp, params, MLP_PARAMS * sizeof(float), cudaMemcpyDefault), "proposal network");
+        if (!bt->have_mlp && bt->exec) {  // the graph was captured without the network
+            cudaGraphExecDestroy(bt->exec);
+            bt->exec = nullptr;
+        }
+        bt->have_mlp = true;
+    }
+    if (margin != bt->margin && bt->exec) {  // the graph holds the margin as an argument
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    bt->margin = margin;
+    for (fbl_solver *s : bt->sv) s->p.proposal = enable ? 1 : 0;
+    return FBL_OK;
+}
+
+namespace {
+
+fbl_status batch_load(fbl_batch *bt, void *const *x, const void *const *b, std::vector<char> &x_dev,
+                      std::vector<char> &b_dev, cudaStream_t cs) {
+    x_dev.assign(bt->n_vol, 0);
+    b_dev.assign(bt->n_vol, 0);
+    for (int v = 0; v < bt->n_vol; ++v) {
+        if (!x[v] || !b[v]) return fail(FBL_E_INVAL, "fblisa_batch: null x or b of volume %d", v);
+        x_dev[v] = is_device_ptr(x[v]);
+        b_dev[v] = is_device_ptr(b[v]);
+    }
+    for (int v = 0; v < bt->n_vol; ++v) {
+        fbl_status st = solver_load_x(bt->sv[v], x[v], x_dev[v], cs);
+        if (st) return st;
+    }
+    return FBL_OK;
+}
+
+fbl_status batch_store(fbl_batch *bt, void *const *x, const std::vector<char> &x_dev, cudaStream_t cs) {
+    for (int v = 0; v < bt->n_vol; ++v) {
+        fbl_status st = solver_store_x(bt->sv[v], x[v], x_dev[v], cs);
+        if (st) return st;
+    }
+    return FBL_OK;
+}
+
+}  // namespace
+
+extern "C" fbl_status fblisa_batch_step(fbl_batch *bt, void *const *x, const void *const *b,
+                                        fbl_step_stats *stats, void *stream) {
+    if (!bt || !x || !b) return fail(FBL_E_INVAL, "fblisa_batch_step: null argument");
+    fbl_status st = check_device(bt->device);
+    if (st) return st;
+    for (fbl_solver *s : bt->sv)
+        if (s->p.proposal && !bt->have_mlp)
+            return fail(FBL_E_INVAL, "fblisa_batch_step: proposal enabled but no network set");
+    cudaStream_t cs = (cudaStream_t)stream;
+    std::vector<char> x_dev, b_dev;
+    if ((st = batch_load(bt, x, b, x_dev, b_dev, cs))) return st;
+    fbl_status rc = batch_iterate(bt, b, b_dev.data(), stats, cs);
+    std::string keep = g_last_error;
+    st = batch_store(bt, x, x_dev, cs);
+    if (rc) {
+        g_last_error = keep;
+        return rc;
+    }
+    return st;
+}
+
+extern "C" fbl_status fblisa_batch_run(fbl_batch *bt, void *const *x, const void *const *b,
+                                       int32_t iterations, fbl_step_stats *trace, int64_t trace_cap,
+                                       int64_t *n_steps, void *stream) {
+    if (!bt || !x || !b) return fail(FBL_E_INVAL, "fblisa_batch_run: null argument");
+    if (iterations < 0 || trace_cap < 0) return fail(FBL_E_INVAL, "fblisa_batch_run: negative count");
+    fbl_status st = check_device(bt->device);
+    if (st) return st;
+    for (fbl_solver *s : bt->sv)
+        if (s->p.proposal && !bt->have_mlp)
+            return fail(FBL_E_INVAL, "fblisa_batch_run: proposal enabled but no network set");
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (n_steps) *n_steps = 0;
+    std::vector<char> x_dev, b_dev;
+    if ((st = batch_load(bt, x, b, x_dev, b_dev, cs))) return st;
+    std::vector<fbl_step_stats> rec(bt->n_vol);
+    fbl_status rc = FBL_OK;
+    int64_t done = 0;
+    for (int32_t it = 0; it < iterations; ++it) {
+        rc = batch_iterate(bt, b, b_dev.data(), rec.data(), cs);
+        if (trace && done < trace_cap)
+            std::memcpy(trace + (size_t)done * bt->n_vol, rec.data(), bt->n_vol * sizeof(fbl_step_stats));
+        if (rc) break;
+        ++done;
+    }
+    if (n_steps) *n_steps = done;
+    std::string keep = g_last_error;
+    st = batch_store(bt, x, x_dev, cs);
+    if (rc) {
+        g_last_error = keep;
+        return rc;
+    }
+    return st;
+}
+
+extern "C" fbl_status fblisa_batch_info(const fbl_batch *bt, int32_t *launch_cfg, int64_t *launches) {
+    if (!bt) return fail(FBL_E_INVAL, "fblisa_batch_info: null batch");
+    if (launch_cfg) {
+        launch_cfg[0] = bt->cols;
+        launch_cfg[1] = bt->split;
+        launch_cfg[2] = bt->vpl;
+        launch_cfg[3] = bt->ntap;
+    }
+    if (launches) *launches = bt->launches;
+    return FBL_OK;
+}
+
+extern "C" fbl_status fblisa_batch_last_batch(const fbl_batch *bt, int32_t v, int32_t *views, int32_t cap,
+                                              int32_t *n) {
+    if (!bt || v < 0 || v >= bt->n_vol) return fail(FBL_E_INVAL, "fblisa_batch_last_batch: bad volume");
+    return fblisa_last_batch(bt->sv[v], views, cap, n);
+}

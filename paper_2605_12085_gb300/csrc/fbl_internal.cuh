@@ -119,7 +119,7 @@ struct DevGeom {
     // launch configuration (chosen by the autotuner; defaults 8 / 1 / 4)
     int k1_cols;                 // projector: detector columns per block (4 or 8)
     int k1_split;                // projector: unmasked middle phase of the plane loop (0 or 1)
-    int k2_vpl;                  // backprojector: consecutive voxels per lane (2 or 4)
+    int k2_vpl;                  // backprojector: consecutive voxels per lane (2, 4, 8 or 16)
     long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
     const FxCol *colF;           // [n_views][nu] exact fixed-point constants
@@ -233,6 +233,107 @@ cudaError_t launch_ls_decide(LSState *ls, PropState *ps, const double *sc,
 cudaError_t launch_prox_zi_dev(const void *vol, ZLayout L, const float *gzi, const LSState *ls,
                                void *trial, int dtype, double *partials, int *n_partials,
                                cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Batched iteration over several volumes (persistent launches).
+//
+// One FB-LISA iteration of every volume of a batch runs as one launch per
+// phase: each phase's work is a list of tiles (the single-volume kernel's
+// blocks, per volume), volumes laid out largest first; a grid sized to fill
+// the GPU takes tiles from an atomic counter until none is left (no waits).
+// Everything that changes between iterations -- the iterate / trial buffers
+// (swapped on acceptance by the decision kernel), the view lists, N_t and the
+// tile counts -- lives in the device descriptors below, so one captured graph
+// serves every iteration.
+
+// One volume of the batch (device memory; the host rewrites it each iteration).
+struct BatchVol {
+    DevGeom g;
+    ZLayout L;
+    void *x_cur, *x_trial;        // current iterate and trial point (library layout)
+    const void *b;                // data: [n_views][nv][nu] (b_views != NULL) or the batch's views
+    const int32_t *b_views;       // slot s -> view index inside b, or NULL
+    const int32_t *views;         // this iteration's views (N_t)
+    float *rt;                    // weighted residual rt[s][iu][RT_PAD + iv]
+    float *grad;                  // gradient [j][i][k]
+    double *partials;             // per-tile partial sums
+    double *sc;                   // [8] scalars (rho0, gTd, dd, l1, rho1, g2)
+    LSState *ls;                  // line-search state
+    PropState *ps;                // proposal statistics (persistent)
+    float scale;                  // n_theta / N_t
+    int N_t;
+    int proposal;                 // 1: learned first trial, 0: alpha_0
+    int tiles[3];                 // K1, K2, K3 tiles of this volume this iteration
+    int first[3];                 // first tile index of this volume in each phase
+    int rfirst[2];                // this trial round: first K1 / K3 tile (searching volumes only)
+};
+
+struct BatchHdr {
+    int n_vol;
+    int total[3];                 // K1, K2, K3 tiles over all volumes
+    int rtotal[2];                // this trial round: K1 / K3 tiles of the searching volumes
+};
+
+// Index of the volume that owns tile t, given each volume's first tile
+// (non-decreasing over the array; a volume without tiles this time repeats
+// its successor's first index, so the last volume with first <= t owns t).
+template <class F>
+__device__ __forceinline__ int batch_find_by(int n_vol, int t, F first) {
+    int lo = 0, hi = n_vol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first(mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int batch_find(const BatchHdr &h, const BatchVol *v, int ph, int t) {
+    return batch_find_by(h.n_vol, t, [&](int q) { return v[q].first[ph]; });
+}
+// Trial rounds: r = 0 for the objective projection (K1), 1 for the prox (K3).
+__device__ __forceinline__ int batch_find_round(const BatchHdr &h, const BatchVol *v, int r, int t) {
+    return batch_find_by(h.n_vol, t, [&](int q) { return v[q].rfirst[r]; });
+}
+
+// Copy bytes (a multiple of 4, 4-byte aligned) from global to shared memory
+// with nthreads threads; the caller synchronises the block afterwards.
+__device__ __forceinline__ void stage_words(void *dst, const void *src, size_t bytes, int tid,
+                                            int nthreads) {
+    const int n = (int)(bytes / 4);
+    for (int q = tid; q < n; q += nthreads) ((int *)dst)[q] = ((const int *)src)[q];
+}
+
+// A volume still inside its line search (neither accepted nor stopped).
+__device__ __forceinline__ bool batch_searching(const LSState &ls) {
+    return ls.accepted == 0 && ls.status == 0;
+}
+
+// ctr: two ints per launch site, zero before the launch and left zero after it.
+// mode RESID reads x_cur and writes rt; mode NORM reads x_trial of the volumes
+// still searching.  cols: detector columns per block, common to the batch;
+// each volume keeps its own plane-loop form (g.k1_split).
+cudaError_t launch_batch_project(int mode, const BatchHdr *hdr, BatchVol *vols, int x_dtype,
+                                 int b_dtype, int cols, int *ctr, cudaStream_t st);
+// Gradient of every volume (scale and views from the descriptor), with the
+// per-tile sums of the squared gradient; each volume keeps its own voxels per
+// lane (g.k2_vpl); ntap >= every volume's g.ntap.
+cudaError_t launch_batch_backproject(const BatchHdr *hdr, BatchVol *vols, int ntap, int *ctr,
+                                     cudaStream_t st);
+// Prox + (2.3) sums of the volumes still searching, alpha from their state.
+cudaError_t launch_batch_prox(const BatchHdr *hdr, BatchVol *vols, int x_dtype, int *ctr,
+                              cudaStream_t st);
+// sc[slot + c] of every volume (or only those still searching) = the fixed-order
+// sum of its partials[c * tiles + 0 .. tiles) of phase ph, c < ncomp.
+cudaError_t launch_batch_reduce(const BatchHdr *hdr, BatchVol *vols, int n_vol, int ph, int ncomp,
+                                int slot, int searching_only, cudaStream_t st);
+cudaError_t launch_batch_propose(BatchVol *vols, int n_vol, const float *params, float margin,
+                                 cudaStream_t st);
+// Line-search init of every volume, and the first trial round's tile offsets.
+cudaError_t launch_batch_ls_init(BatchHdr *hdr, BatchVol *vols, int n_vol, cudaStream_t st);
+// (2.3) for every volume still searching; on acceptance the volume's x_cur and
+// x_trial are swapped; the next round's tile offsets cover the volumes still
+// searching, and the WHILE condition is set while any volume searches.
+cudaError_t launch_batch_decide(BatchHdr *hdr, BatchVol *vols, int n_vol,
+                                cudaGraphConditionalHandle cond, cudaStream_t st);
 
 // Record the message returned by fbl_last_error() on this thread.
 void set_last_error(const char *msg);

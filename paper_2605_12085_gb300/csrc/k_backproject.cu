@@ -33,6 +33,10 @@ namespace fbl {
 namespace {
 
 constexpr int K2_LANES = 32;
+
+__host__ __device__ __forceinline__ int k2_vpl_of(const DevGeom &g) {
+    return (g.k2_vpl == 2 || g.k2_vpl == 8 || g.k2_vpl == 16) ? g.k2_vpl : 4;
+}
 constexpr int K2_WARPS = 8;   // consecutive i per block
 
 struct BpArgs {
@@ -71,14 +75,16 @@ __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const f
     }
 }
 
+// One block's work: voxel columns i = bx*8 .. bx*8+7 of row j, z-span bz;
+// the block's sum of squared gradient values goes to *g2_partial (if not NULL).
+// Called by every thread.
 template <int NTAP, int K2_VPL>
-__global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
+__device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, double *g2_partial) {
     constexpr int K2_KSPAN = K2_LANES * K2_VPL;
     const DevGeom &g = a.g;
     const int lane = threadIdx.x;
-    const int i = blockIdx.x * K2_WARPS + threadIdx.y;  // uniform over the warp
-    const int j = blockIdx.y;
-    const int kfirst = blockIdx.z * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+VPL-1
+    const int i = bx * K2_WARPS + threadIdx.y;  // uniform over the warp
+    const int kfirst = bz * K2_KSPAN + K2_VPL * lane;  // this lane: kfirst .. kfirst+VPL-1
     float acc[K2_VPL];
 #pragma unroll
     for (int q = 0; q < K2_VPL; ++q) acc[q] = 0.f;
@@ -145,20 +151,78 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArg
             }
         }
     }
-    if (a.g2_partials) {
+    if (g2_partial) {
         float vv[1] = {g2};
         double o[1];
         block_sum_f64<K2_LANES * K2_WARPS, 1>(vv, o);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            a.g2_partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = o[0];
+        if (threadIdx.x == 0 && threadIdx.y == 0) *g2_partial = o[0];
+    }
+}
+
+template <int NTAP, int K2_VPL>
+__global__ void __launch_bounds__(K2_LANES *K2_WARPS) k2_backproject(const BpArgs a) {
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    k2_tile<NTAP, K2_VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
+}
+
+// Persistent batched backprojector: the blocks of k2_backproject of every
+// volume, taken from an atomic counter.  Each volume keeps its own voxels per
+// lane (its geometry's k2_vpl, a warp-uniform switch).  Registers are capped
+// at 48 (5 blocks per SM), as for the batched projector.
+template <int NTAP>
+__global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const BatchHdr *hdr,
+                                                                        const BatchVol *vols, int *ctr) {
+    __shared__ int s_tile;
+    __shared__ BpArgs sa;
+    const int tid = threadIdx.x + K2_LANES * threadIdx.y;
+    const int total = hdr->total[1];
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        const int vi = batch_find(*hdr, vols, 1, t);
+        const BatchVol &bv = vols[vi];
+        // the volume's arguments, staged in shared memory for the whole block
+        stage_words(&sa.g, &bv.g, sizeof(DevGeom), tid, K2_LANES * K2_WARPS);
+        if (tid == 0) {
+            sa.rt = bv.rt;
+            sa.views = bv.views;
+            sa.n_sel = bv.N_t;
+            sa.scale = bv.scale;
+            sa.gzi = bv.grad;
+            sa.g2_partials = bv.partials;
+        }
+        __syncthreads();
+        const BpArgs &a = sa;
+        const int local = t - bv.first[1];
+        const int vpl = k2_vpl_of(bv.g);
+        const int gx = (bv.g.nx + K2_WARPS - 1) / K2_WARPS;
+        const int bx = local % gx;
+        const int rest = local / gx;
+        const int j = rest % bv.g.ny;
+        const int bz = rest / bv.g.ny;
+        double *part = bv.partials + local;
+        switch (vpl) {
+            case 2: k2_tile<NTAP, 2>(a, bx, j, bz, part); break;
+            case 8: k2_tile<NTAP, 8>(a, bx, j, bz, part); break;
+            case 16: k2_tile<NTAP, 16>(a, bx, j, bz, part); break;
+            default: k2_tile<NTAP, 4>(a, bx, j, bz, part); break;
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(ctr + 1, 1) == (int)gridDim.x - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
     }
 }
 
 }  // namespace
 
-static int k2_vpl_of(const DevGeom &g) {
-    return (g.k2_vpl == 2 || g.k2_vpl == 8 || g.k2_vpl == 16) ? g.k2_vpl : 4;
-}
 
 int backproject_num_partials(const DevGeom &g) {
     const int vpl = k2_vpl_of(g);
@@ -172,6 +236,37 @@ static void launch_k2(int vpl, dim3 grid, dim3 block, cudaStream_t st, const BpA
         case 8: k2_backproject<NT, 8><<<grid, block, 0, st>>>(a); break;
         case 16: k2_backproject<NT, 16><<<grid, block, 0, st>>>(a); break;
         default: k2_backproject<NT, 4><<<grid, block, 0, st>>>(a); break;
+    }
+}
+
+template <class K>
+static int k2_persistent_grid(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, K2_LANES * K2_WARPS, 0);
+    return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
+template <int NT>
+static cudaError_t launch_kb2(const BatchHdr *hdr, BatchVol *vols, int *ctr, cudaStream_t st) {
+    auto k = kb_backproject<NT>;
+    static const int grid = k2_persistent_grid(k);
+    k<<<grid, dim3(K2_LANES, K2_WARPS), 0, st>>>(hdr, vols, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_backproject(const BatchHdr *hdr, BatchVol *vols, int ntap, int *ctr,
+                                     cudaStream_t st) {
+    switch (ntap) {
+        case 1: return launch_kb2<1>(hdr, vols, ctr, st);
+        case 2: return launch_kb2<2>(hdr, vols, ctr, st);
+        case 3: return launch_kb2<3>(hdr, vols, ctr, st);
+        case 4: return launch_kb2<4>(hdr, vols, ctr, st);
+        case 5: return launch_kb2<5>(hdr, vols, ctr, st);
+        case 6: return launch_kb2<6>(hdr, vols, ctr, st);
+        case 7: return launch_kb2<7>(hdr, vols, ctr, st);
+        default: return launch_kb2<8>(hdr, vols, ctr, st);
     }
 }
 

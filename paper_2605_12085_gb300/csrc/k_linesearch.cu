@@ -46,10 +46,10 @@ __device__ void proposal_features(const LSState &ls, const PropState &ps, double
 
 // One warp: features, the network (hidden units l and l+32 per lane), the
 // first trial step.  ls->alpha_init holds alpha_0 on entry.
-__global__ void k_propose(LSState *ls, const PropState *ps, const double *sc, const float *params,
-                          float margin) {
+__device__ __forceinline__ void propose_warp(LSState *ls, const PropState *ps, const double *sc,
+                                             const float *params, float margin) {
     __shared__ float x[MLP_IN], h1[MLP_HIDDEN];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const double rho0 = sc[0], g2 = sc[5];
     const double f = __dmul_rn(__dmul_rn(0.5, ls->scale), rho0);
     if (lane == 0) proposal_features(*ls, *ps, f, g2, x);
@@ -97,9 +97,52 @@ __global__ void k_propose(LSState *ls, const PropState *ps, const double *sc, co
     }
 }
 
-// sc: [rho0, gTd, dd, l1, rho1] as reduced by the preceding kernels.
-__global__ void k_ls_decide(LSState *ls, PropState *ps, const double *sc,
-                            cudaGraphConditionalHandle cond) {
+__global__ void k_propose(LSState *ls, const PropState *ps, const double *sc, const float *params,
+                          float margin) {
+    propose_warp(ls, ps, sc, params, margin);
+}
+
+// One block of 32 threads per volume of a batch.
+__global__ void kb_propose(const BatchVol *vols, const float *params, float margin) {
+    const BatchVol &bv = vols[blockIdx.x];
+    propose_warp(bv.ls, bv.ps, bv.sc, bv.proposal ? params : nullptr, margin);
+}
+
+// Tile offsets of the next trial round over the volumes still searching
+// (thread 0, after the block has updated every volume's state).
+__device__ void batch_round_offsets(BatchHdr *hdr, BatchVol *vols, int n_vol) {
+    int acc[2] = {0, 0};
+    for (int v = 0; v < n_vol; ++v) {
+        BatchVol &bv = vols[v];
+        const bool on = batch_searching(*bv.ls);
+        bv.rfirst[0] = acc[0];
+        bv.rfirst[1] = acc[1];
+        if (on) {
+            acc[0] += bv.tiles[0];
+            acc[1] += bv.tiles[2];
+        }
+    }
+    hdr->rtotal[0] = acc[0];
+    hdr->rtotal[1] = acc[1];
+}
+
+// One block, one thread per volume.
+__global__ void kb_ls_init(BatchHdr *hdr, BatchVol *vols, int n_vol) {
+    const int v = threadIdx.x;
+    if (v < n_vol) {
+        LSState *ls = vols[v].ls;
+        ls->alpha = ls->alpha_init;
+        ls->trials = 0;
+        ls->accepted = 0;
+        ls->status = FBL_OK;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) batch_round_offsets(hdr, vols, n_vol);
+}
+
+// sc: [rho0, gTd, dd, l1, rho1] as reduced by the preceding kernels.  Returns
+// 1 when another trial is needed.
+__device__ __forceinline__ unsigned int ls_decide_one(LSState *ls, PropState *ps, const double *sc) {
     const double rho0 = sc[0], gTd = sc[1], dd = sc[2], rho1 = sc[4];
     const double alpha = ls->alpha;
     const double half_scale = __dmul_rn(0.5, ls->scale);
@@ -133,21 +176,51 @@ __global__ void k_ls_decide(LSState *ls, PropState *ps, const double *sc,
         ls->alpha = __dmul_rn(alpha, ls->beta);
         more = 1;
     }
-    cudaGraphSetConditional(cond, more);
+    return more;
+}
+
+__global__ void k_ls_decide(LSState *ls, PropState *ps, const double *sc,
+                            cudaGraphConditionalHandle cond) {
+    cudaGraphSetConditional(cond, ls_decide_one(ls, ps, sc));
+}
+
+// One thread per volume of a batch (a single block): (2.3) for the volumes
+// still searching; an accepted volume's trial point becomes its iterate.
+__global__ void kb_decide(BatchHdr *hdr, BatchVol *vols, int n_vol, cudaGraphConditionalHandle cond) {
+    const int v = threadIdx.x;
+    unsigned int more = 0;
+    if (v < n_vol) {
+        BatchVol &bv = vols[v];
+        if (batch_searching(*bv.ls)) {
+            more = ls_decide_one(bv.ls, bv.ps, bv.sc);
+            if (bv.ls->accepted) {
+                void *t = bv.x_cur;
+                bv.x_cur = bv.x_trial;
+                bv.x_trial = t;
+            }
+        }
+    }
+    const int any = __syncthreads_or(more);
+    if (threadIdx.x == 0) {
+        batch_round_offsets(hdr, vols, n_vol);
+        cudaGraphSetConditional(cond, any ? 1u : 0u);
+    }
 }
 
 // Prox + reductions with the step taken from the line-search state.
 constexpr int PZ_TX = 64;
 constexpr int PZ_TY = 4;
 
+// One block's rows (PZ_TY (i, j) columns from blk * PZ_TY) of the prox, with
+// its three sums written to partials[c * nblk + blk].  Called by every thread.
 template <typename T>
-__global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi_dev(const T *__restrict__ vol, ZLayout L,
-                                                              const float *__restrict__ gzi,
-                                                              const LSState *ls, T *__restrict__ trial,
-                                                              double *__restrict__ partials) {
+__device__ __forceinline__ void prox_tile(const T *__restrict__ vol, const ZLayout &L,
+                                          const float *__restrict__ gzi, const LSState *ls,
+                                          T *__restrict__ trial, double *__restrict__ partials,
+                                          int blk, int nblk) {
     const double a = ls->alpha;
     const float alpha = (float)a, amu = (float)(a * ls->mu);
-    const int row = blockIdx.x * PZ_TY + threadIdx.y;
+    const int row = blk * PZ_TY + threadIdx.y;
     float sums[3] = {0.f, 0.f, 0.f};
     if (row < L.nx * L.ny) {
         const int j = row / L.nx, i = row - j * L.nx;
@@ -171,14 +244,90 @@ __global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi_dev(const T *__restric
     double out[3];
     block_sum_f64<PZ_TX * PZ_TY, 3>(sums, out);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const size_t nblk = gridDim.x;
-        partials[blockIdx.x] = out[0];
-        partials[nblk + blockIdx.x] = out[1];
-        partials[2 * nblk + blockIdx.x] = out[2];
+        partials[blk] = out[0];
+        partials[(size_t)nblk + blk] = out[1];
+        partials[2 * (size_t)nblk + blk] = out[2];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi_dev(const T *__restrict__ vol, ZLayout L,
+                                                              const float *__restrict__ gzi,
+                                                              const LSState *ls, T *__restrict__ trial,
+                                                              double *__restrict__ partials) {
+    prox_tile<T>(vol, L, gzi, ls, trial, partials, blockIdx.x, gridDim.x);
+}
+
+// Persistent batched prox over the volumes still searching.
+template <typename T>
+__global__ void __launch_bounds__(PZ_TX *PZ_TY) kb_prox(const BatchHdr *hdr, const BatchVol *vols,
+                                                        int *ctr) {
+    __shared__ int s_tile;
+    const int tid = threadIdx.x + PZ_TX * threadIdx.y;
+    const int total = hdr->rtotal[1];
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        const BatchVol &bv = vols[batch_find_round(*hdr, vols, 1, t)];
+        const int local = t - bv.rfirst[1];
+        prox_tile<T>((const T *)bv.x_cur, bv.L, bv.grad, bv.ls, (T *)bv.x_trial, bv.partials, local,
+                     bv.tiles[2]);
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(ctr + 1, 1) == (int)gridDim.x - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
     }
 }
 
 }  // namespace
+
+cudaError_t launch_batch_propose(BatchVol *vols, int n_vol, const float *params, float margin,
+                                 cudaStream_t st) {
+    kb_propose<<<n_vol, 32, 0, st>>>(vols, params, margin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ls_init(BatchHdr *hdr, BatchVol *vols, int n_vol, cudaStream_t st) {
+    if (n_vol < 1 || n_vol > 1024) return cudaErrorInvalidValue;
+    kb_ls_init<<<1, (n_vol + 31) / 32 * 32, 0, st>>>(hdr, vols, n_vol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_decide(BatchHdr *hdr, BatchVol *vols, int n_vol, cudaGraphConditionalHandle cond,
+                                cudaStream_t st) {
+    if (n_vol < 1 || n_vol > 1024) return cudaErrorInvalidValue;
+    kb_decide<<<1, (n_vol + 31) / 32 * 32, 0, st>>>(hdr, vols, n_vol, cond);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_kb_prox(const BatchHdr *hdr, BatchVol *vols, int *ctr, cudaStream_t st) {
+    static const int grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_prox<T>, PZ_TX * PZ_TY, 0);
+        return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }();
+    kb_prox<T><<<grid, dim3(PZ_TX, PZ_TY), 0, st>>>(hdr, vols, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prox(const BatchHdr *hdr, BatchVol *vols, int x_dtype, int *ctr,
+                              cudaStream_t st) {
+    switch (x_dtype) {
+        case FBL_BF16: return launch_kb_prox<__nv_bfloat16>(hdr, vols, ctr, st);
+        case FBL_F16: return launch_kb_prox<__half>(hdr, vols, ctr, st);
+        default: return launch_kb_prox<float>(hdr, vols, ctr, st);
+    }
+}
 
 cudaError_t launch_ls_init(LSState *ls, cudaStream_t st) {
     k_ls_init<<<1, 1, 0, st>>>(ls);

@@ -190,11 +190,10 @@ __global__ void __launch_bounds__(F_NT) k_norms(const T *__restrict__ x, const T
 
 constexpr int R_NT = 1024;
 
-__global__ void __launch_bounds__(R_NT) k_reduce(const double *__restrict__ partials, int n,
-                                                 int stride, double *__restrict__ out) {
+// Fixed-order FP64 sum of p[0 .. n) by one block of R_NT threads; the result
+// is valid in thread 0.
+__device__ __forceinline__ double block_reduce_fixed(const double *__restrict__ p, int n) {
     __shared__ double sm[R_NT];
-    const int c = blockIdx.x;
-    const double *p = partials + (size_t)c * stride;
     double s = 0.0;
     for (int q = threadIdx.x; q < n; q += R_NT) s += p[q];
     sm[threadIdx.x] = s;
@@ -203,7 +202,26 @@ __global__ void __launch_bounds__(R_NT) k_reduce(const double *__restrict__ part
         if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[c] = sm[0];
+    return sm[0];
+}
+
+__global__ void __launch_bounds__(R_NT) k_reduce(const double *__restrict__ partials, int n,
+                                                 int stride, double *__restrict__ out) {
+    const int c = blockIdx.x;
+    const double s = block_reduce_fixed(partials + (size_t)c * stride, n);
+    if (threadIdx.x == 0) out[c] = s;
+}
+
+// One block per (volume, component): the same fixed order as k_reduce over the
+// volume's tiles of phase ph (stride = its tile count).
+__global__ void __launch_bounds__(R_NT) kb_reduce(const BatchVol *vols, int ph, int ncomp, int slot,
+                                                  int searching_only) {
+    const int v = blockIdx.x / ncomp, c = blockIdx.x % ncomp;
+    const BatchVol &bv = vols[v];
+    if (searching_only && !batch_searching(*bv.ls)) return;  // block-uniform
+    const int n = bv.tiles[ph];
+    const double s = block_reduce_fixed(bv.partials + (size_t)c * n, n);
+    if (threadIdx.x == 0) bv.sc[slot + c] = s;
 }
 
 }  // namespace
@@ -327,6 +345,13 @@ cudaError_t launch_norms(const void *x, const void *xr, int dtype, int64_t n, do
             break;
         default: k_norms<<<nb, F_NT, 0, st>>>((const float *)x, (const float *)xr, n, partials); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(const BatchHdr *hdr, BatchVol *vols, int n_vol, int ph, int ncomp,
+                                int slot, int searching_only, cudaStream_t st) {
+    (void)hdr;
+    kb_reduce<<<n_vol * ncomp, R_NT, 0, st>>>(vols, ph, ncomp, slot, searching_only);
     return cudaGetLastError();
 }
 

@@ -105,6 +105,21 @@ WORKLOADS: Dict[str, Workload] = {
 }
 
 
+def batched_small_workloads() -> List[Workload]:
+    """16 small uneven volumes, the batched workload scaled down by 4 in edge
+    (N_i = round(24 + 56 i/15), 30 + 6 i views, detector ceil(1.5 N_i)^2):
+    the regime where one volume alone cannot fill the GPU."""
+    out = []
+    for i in range(16):
+        n = int(round(24 + 56 * i / 15))
+        views = 30 + 6 * i
+        det = int(math.ceil(1.5 * n))
+        out.append(Workload(f"c5s_{i}", _cube(n, views, det), 8, 0, 0.0, "gaussian", 0.01, 0.0,
+                            N0=int(math.ceil(views / 12)), epochs=2, seed_phantom=1200 + i,
+                            seed_noise=2200 + i, seed_batches=3200 + i))
+    return out
+
+
 def batched_workloads() -> List[Workload]:
     """The 16 uneven volumes of the batched workload: N_i = round(96 + 224 i/15),
     120 + 24 i views, detector ceil(1.5 N_i) square."""
