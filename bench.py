@@ -378,7 +378,8 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
             k += 1
             trials += st["backtracks"] + 1
             if k % check_every == 0 or k == n_iter:
-                F, _, re = fbl.evaluate(G, x, b, wl.mu, x_true=xt_d)
+                # BF16 -> FP32 widening is exact, so F is that of the stored iterate
+                F, _, re = fbl.evaluate(G, x.float() if fast else x, b, wl.mu, x_true=xt_d)
                 hist.append((k, elapsed, F, re))
                 if target is not None and F <= target:
                     break

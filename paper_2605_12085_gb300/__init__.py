@@ -290,7 +290,10 @@ def residual_norm(geom: Geometry, x, views: Sequence[int], b, stream=None) -> fl
 
 
 def evaluate(geom: Geometry, x, b, mu: float, x_true=None, stream=None):
-    """(F(x), 1/2||Ax-b||^2, RE) over all views (RE = 0 without x_true)."""
+    """(F(x), 1/2||Ax-b||^2, RE) over all views (RE = 0 without x_true);
+    x_true must have x's dtype."""
+    if x_true is not None and _dtype_code(x_true) != _dtype_code(x):
+        raise ValueError("evaluate: x_true must have the dtype of x")
     out = (ctypes.c_double * 3)()
     _check(lib.evaluate(geom.handle, _ptr(x), _dtype_code(x), _ptr(b), _dtype_code(b), float(mu),
                         None if x_true is None else _ptr(x_true), out,
