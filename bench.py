@@ -62,6 +62,8 @@ def parse():
                     help="epochs of plain FP32 that define F* (0: skip time-to-objective)")
     ap.add_argument("--tto-check", type=int, default=3, help="iterations between F evaluations")
     ap.add_argument("--batched", type=int, default=1, help="also time the 16-volume batched launch")
+    ap.add_argument("--c5b", type=int, default=0,
+                    help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     return ap.parse_args()
 
 
@@ -180,6 +182,56 @@ def batched_record(fbl, device, wls, label, proposal=False, steps=5, warmup=3):
                               "k2_vpl": [t["k2_vpl"] for t in tunes]},
             "backtracks_per_volume_iteration":
                 statistics.mean(st["backtracks"] for rec in b_recs for st in rec)}
+
+
+def c5b_record(fbl, device, steps=5, warmup=2):
+    """The large configuration: 1024^3 volume, 1440 views, 1536^2 detector,
+    60-view mini-batches; FP16 storage (FP32 accumulation, FP64 line-search
+    sums) with the learned step proposal and graph-captured iterations, next
+    to plain FP16 and plain FP32 iterations of the same problem."""
+    import torch
+    import synth
+    from paper_2605_12085_gb300 import proposal as prop
+    wl = synth.WORKLOADS["c5b_1024"]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    del xt
+    tune = fbl.geometry_autotune(G, fbl.F16, wl.N0)
+    net, _ = prop.load()
+    stream = torch.cuda.current_stream(device)
+    out = {"workload": "c5b_1024: 1024^3 volume, 1440 views, 1536x1536 detector, mini-batch 60 views",
+           "autotune_f16": tune}
+    for name, code, td, learned, graph in (("f16_learned_graph", fbl.F16, torch.float16, True, 1),
+                                           ("f16_plain", fbl.F16, torch.float16, False, 0),
+                                           ("f32_plain", fbl.F32, torch.float32, False, 0)):
+        bv = b if code == fbl.F32 else b.to(td)
+        p = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
+                               x_dtype=code, b_dtype=code, use_graph=graph)
+        S = fbl.fblisa_create(G, p)
+        if learned:
+            S.set_proposal(net)
+        x = torch.zeros(g.vol_shape, dtype=td, device=device)
+        for _ in range(warmup):
+            S.step(x, bv)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = [S.step(x, bv) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / steps
+        units = sum(step_units(r, g) for r in st) / steps
+        out[name] = {"ms_per_iteration": ms, "gups": units / (ms * 1e-3) / 1e9,
+                     "trials_per_iteration": statistics.mean(r["backtracks"] + 1 for r in st),
+                     "steps": steps, "warmup": warmup}
+        del S, x
+        if bv is not b:
+            del bv
+        torch.cuda.empty_cache()
+    del b, G
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_records(fbl, device):
@@ -535,6 +587,9 @@ def run_ours(args, rank, world, local_rank):
 
     if args.batched and rank == 0:
         out["batched"] = batched_records(fbl, device)
+
+    if args.c5b and rank == 0:
+        out["c5b"] = c5b_record(fbl, device)
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,

@@ -82,9 +82,9 @@ class Workload:
     mu: float = 1.0
 
 
-def _cube(n: int, n_views: int, det: int) -> Geometry:
-    return Geometry(nx=n, ny=n, nz=n, vx=1.0, vy=1.0, vz=1.0, n_views=n_views,
-                    sod=1000.0, sdd=1500.0, nu=det, nv=det, du=1.5, dv=1.5)
+def _cube(n: int, n_views: int, det: int, voxel: float = 1.0) -> Geometry:
+    return Geometry(nx=n, ny=n, nz=n, vx=voxel, vy=voxel, vz=voxel, n_views=n_views,
+                    sod=1000.0, sdd=1500.0, nu=det, nv=det, du=1.5 * voxel, dv=1.5 * voxel)
 
 
 # The five synthetic workloads.  Detector pixels are 1.5 mm and SDD/SOD = 1.5,
@@ -99,7 +99,9 @@ WORKLOADS: Dict[str, Workload] = {
     # a profiling-sized case: volume larger than L2, a few GB on the device in all
     "p384": Workload("p384", _cube(384, 120, 576), 40, 0, 0.0, "gaussian", 0.01, 0.0,
                      N0=20, epochs=2, seed_phantom=1009, seed_noise=2009, seed_batches=3009),
-    "c5b_1024": Workload("c5b_1024", _cube(1024, 1440, 1536), 100, 0, 0.0, "gaussian", 0.01,
+    # 1024 voxels of 1 mm would not fit between source and detector (circumradius
+    # 724 mm > SDD - SOD = 500 mm): the 512^3 geometry at twice the resolution
+    "c5b_1024": Workload("c5b_1024", _cube(1024, 1440, 1536, voxel=0.5), 100, 0, 0.0, "gaussian", 0.01,
                          0.0, N0=60, epochs=10, seed_phantom=1005, seed_noise=2005,
                          seed_batches=3005),
 }
