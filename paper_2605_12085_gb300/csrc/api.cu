@@ -99,6 +99,8 @@ struct fbl_geometry {
     float4 *d_colB = nullptr;
     FxCol *d_colF = nullptr;
     float2 *d_trig = nullptr;
+    int *d_err = nullptr;   // status word of the TMA-staged projector's bounded waits
+    int *h_err = nullptr;   // pinned mirror
 };
 
 namespace {
@@ -106,6 +108,18 @@ namespace {
 ZLayout layout_for(const fbl_geometry *g, int dtype) {
     const fbl_geometry_desc &d = g->desc;
     return make_layout(d.nx, d.ny, d.nz, dtype_size(dtype));
+}
+
+// After work on stream st that used the TMA-staged projector: FBL_E_TIMEOUT
+// (and the word cleared) if one of its bounded waits gave up.  Synchronises st.
+fbl_status check_timeout(const fbl_geometry *g, const DevGeom &dg, cudaStream_t st) {
+    if (dg.k1_split != 2 || !g->d_err) return FBL_OK;
+    if (cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return FBL_OK;  // the caller's next CUDA call reports the error
+    if (*g->h_err == 0) return FBL_OK;
+    cudaMemsetAsync(g->d_err, 0, sizeof(int), st);
+    return FBL_E_TIMEOUT;
 }
 
 double view_angle(const fbl_geometry_desc &d, const std::vector<double> &ang, int v) {
@@ -294,6 +308,9 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     if (e == cudaSuccess) e = cudaMemcpy(g->d_colA, colA.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_colB, colB.data(), ncol * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_trig, trig.data(), d.n_views * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_err, sizeof(int));
     if (e != cudaSuccess) {
         geometry_destroy(g);
         return cuda_fail(e, "geometry_create: device tables");
@@ -302,6 +319,7 @@ extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometr
     dg.colF = g->d_colF;
     dg.colB = g->d_colB;
     dg.trig = g->d_trig;
+    dg.err = g->d_err;
     *out = g;
     return FBL_OK;
 }
@@ -315,6 +333,8 @@ extern "C" void geometry_destroy(fbl_geometry *g) {
     cudaFree(g->d_colB);
     cudaFree(g->d_trig);
     cudaFree(g->d_colF);
+    cudaFree(g->d_err);
+    cudaFreeHost(g->h_err);
     if (g->device >= 0 && cur >= 0 && cur != g->device) cudaSetDevice(cur);
     delete g;
 }
@@ -591,6 +611,7 @@ extern "C" fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_
     CK(cudaMemcpyAsync(rho_host, res.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
     CK(cudaStreamSynchronize(s), "residual_norm");
     if (!std::isfinite(*rho_host)) return fail(FBL_E_NONFINITE, "residual_norm: non-finite result");
+    if ((st = check_timeout(g, g->dg, s))) return fail(st, "residual_norm: a bounded wait of the projector gave up");
     return FBL_OK;
 }
 
@@ -645,6 +666,7 @@ extern "C" fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_d
     std::vector<double> h(nchunks + 3);
     CK(cudaMemcpyAsync(h.data(), res.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
     CK(cudaStreamSynchronize(s), "evaluate");
+    if ((st = check_timeout(g, g->dg, s))) return fail(st, "evaluate: a bounded wait of the projector gave up");
     double rho = 0.0;
     for (int c = 0; c < nchunks; ++c) rho += h[c];
     out3_host[1] = 0.5 * rho;
@@ -1010,6 +1032,10 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         CK(cudaMemcpyAsync(s->d_ls, s->h_ls, sizeof(LSState), cudaMemcpyHostToDevice, st), "line-search state");
         CK(cudaGraphLaunch(ge->exec, st), "graph launch");
         CK(cudaStreamSynchronize(st), "graph iteration");
+        if (check_timeout(g, s->dg, st)) {
+            restore();
+            return fail(FBL_E_TIMEOUT, "fblisa_step: a bounded wait of the projector gave up");
+        }
         const LSState r = *s->h_ls;
         const int trials = r.trials + 1;
         s->prof_launches[0] += 1;
@@ -1156,6 +1182,10 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         return fail(FBL_E_LINESEARCH, "fblisa_step: no step passed (2.3) within %d backtracks",
                     s->p.max_backtracks);
     }
+    if (check_timeout(g, s->dg, st)) {
+        restore();
+        return fail(FBL_E_TIMEOUT, "fblisa_step: a bounded wait of the projector gave up");
+    }
     // Step 2d: x <- x_bar (swap the state and trial buffers); the next first
     // trial is alpha_0 again, or the proposal's
     std::swap(s->st, s->tr);
@@ -1261,8 +1291,10 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
     };
     float best = 1e30f;
     int qi = 0;
-    for (int cols : {8, 4})
-        for (int split : {1, 0}) {
+    const int k1_cfg[5][2] = {{8, 1}, {8, 0}, {4, 1}, {4, 0}, {8, 2}};  // (columns, plane-loop form)
+    for (const auto &cfg : k1_cfg) {
+        {
+            const int cols = cfg[0], split = cfg[1];
             DevGeom t = dg;
             t.k1_cols = cols;
             t.k1_split = split;
@@ -1274,12 +1306,17 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
                                           st);
                 },
                 ms);
+            if (e == cudaErrorNotSupported && split == 2) {  // no tensor-map support: not a candidate
+                cudaGetLastError();
+                ++qi;
+                continue;
+            }
             if (e != cudaSuccess) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 return cuda_fail(e, "autotune projector");
             }
-            if (rep && qi < 4) rep->k1_ms[qi] = ms;
+            if (rep && qi < 5) rep->k1_ms[qi] = ms;
             ++qi;
             if (ms < best) {
                 best = ms;
@@ -1287,6 +1324,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
                 dg.k1_split = split;
             }
         }
+    }
     best = 1e30f;
     qi = 0;
     for (int vpl : {4, 2, 8, 16}) {
@@ -1383,10 +1421,10 @@ extern "C" fbl_status mlp_train(float *params, float *adam_m, float *adam_v, int
 extern "C" fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                           int32_t k2_vpl) {
     if (!g) return fail(FBL_E_INVAL, "geometry_set_launch: null geometry");
-    if ((k1_cols != 4 && k1_cols != 8) || (k1_split != 0 && k1_split != 1) ||
+    if ((k1_cols != 4 && k1_cols != 8) || (k1_split < 0 || k1_split > 2) ||
         (k2_vpl != 2 && k2_vpl != 4 && k2_vpl != 8 && k2_vpl != 16))
         return fail(FBL_E_INVAL,
-                    "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1}, k2_vpl in {2,4,8,16}");
+                    "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1,2}, k2_vpl in {2,4,8,16}");
     g->dg.k1_cols = k1_cols;
     g->dg.k1_split = k1_split;
     g->dg.k2_vpl = k2_vpl;

@@ -118,13 +118,14 @@ struct DevGeom {
     int ntap;                    // detector rows that can touch one voxel in one column
     // launch configuration (chosen by the autotuner; defaults 8 / 1 / 4)
     int k1_cols;                 // projector: detector columns per block (4 or 8)
-    int k1_split;                // projector: unmasked middle phase of the plane loop (0 or 1)
+    int k1_split;                // projector plane loop: 0 masked, 1 unmasked middle phase, 2 TMA-staged bricks
     int k2_vpl;                  // backprojector: consecutive voxels per lane (2, 4, 8 or 16)
     long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
     const FxCol *colF;           // [n_views][nu] exact fixed-point constants
     const float4 *colB;          // [n_views][nu] (wa, h2, fam, 0)
     const float2 *trig;          // [n_views] (cos, sin)
+    int *err;                    // device status word: FBL_E_TIMEOUT after a bounded wait gave up
 };
 
 enum ProjMode { PROJ_STORE = 0, PROJ_RESID = 1, PROJ_NORM = 2 };

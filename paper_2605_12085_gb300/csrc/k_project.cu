@@ -25,6 +25,11 @@
 // are FP32; the squared residuals are summed in FP64 across threads and
 // blocks in a fixed order.
 #include <algorithm>
+#include <climits>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <type_traits>
 
 #include "fbl_internal.cuh"
 #include "fbl_reduce.cuh"
@@ -235,6 +240,306 @@ __global__ void __launch_bounds__(32 * COLS) k1_project(const ProjArgs a) {
                                            MODE != PROJ_STORE ? a.partials + blk : nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged projector (launch configuration k1_split = 2).
+//
+// Same rays, crossings and epilogue as k1_tile, but the volume reaches the
+// block through shared memory: the block (8 detector columns x 32 rows of one
+// view) walks its planes in chunks of TMA_P, and for every chunk one thread
+// issues a single cp.async.bulk.tensor.3d copy of the brick that holds every
+// bilinear footprint of the chunk (KZ voxels along z x TMA_KB in-plane rows x
+// TMA_P planes) into one of two buffers while the block samples the previous
+// chunk.  The brick's origin comes from the band's extreme rays of each
+// column, whose crossings are affine in the plane index (exact Q.40), so it
+// is exact; its z origin is rounded down to the 16-byte rule of TMA.  Every
+// sample still checks its indices against the brick and reads the global
+// copy when outside (and so do chunks whose footprint is larger than a brick,
+// and blocks whose columns belong to two ray families).  Every wait on a
+// brick is bounded: past the limit the kernel records FBL_E_TIMEOUT in *err,
+// stops using bricks (global reads, same result) and drains its own copies
+// with a second bounded wait before it exits.
+constexpr int TMA_COLS = 8;
+constexpr int TMA_P = 4;
+constexpr int TMA_KB = 24;
+constexpr int TMA_SPIN = 1 << 22;  // mbarrier polls before a wait gives up
+template <typename TX> struct TmaShape {
+    static constexpr int KZ = sizeof(TX) == 4 ? 56 : 64;  // KZ * sizeof(TX): a multiple of 16 bytes
+    static constexpr int ALIGN = 16 / (int)sizeof(TX);     // z origin alignment, elements
+    static constexpr int BRICK = TMA_P * TMA_KB * KZ;      // elements per brick
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// One bounded wait for the phase with the given parity; false after TMA_SPIN polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (int it = 0; it < TMA_SPIN; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+struct TmaMeta {
+    int klo, blo, mc, ok;  // brick origin (z, in-plane, plane) and whether it was loaded
+};
+
+template <typename TX, typename TB, typename TO, int MODE>
+__global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a,
+                                                                const __grid_constant__ CUtensorMap mapX,
+                                                                const __grid_constant__ CUtensorMap mapY,
+                                                                int *err) {
+    constexpr int KZ = TmaShape<TX>::KZ, ALIGN = TmaShape<TX>::ALIGN, BRICK = TmaShape<TX>::BRICK;
+    constexpr int P = TMA_P, KB = TMA_KB;
+    constexpr unsigned BRICK_BYTES = (unsigned)(BRICK * sizeof(TX));
+    extern __shared__ __align__(128) unsigned char tma_dsm[];
+    // [2][BRICK], 128-byte aligned (the launch adds 128 bytes of slack)
+    TX *bricks = (TX *)(tma_dsm + ((128u - (smem_addr(tma_dsm) & 127u)) & 127u));
+    __shared__ __align__(8) unsigned long long full[2];
+    __shared__ TmaMeta meta[2];
+    __shared__ long long colz[TMA_COLS][4];  // per column: band's lowest / highest row q_z = c0 + m*c1
+    __shared__ long long colb[TMA_COLS][2];  // per column: q_b = c0 + m*c1
+    __shared__ int colfam[TMA_COLS];         // 0 / 1 family, -1 no column
+    __shared__ int s_u0[TMA_COLS], s_u1[TMA_COLS];
+    __shared__ int s_mixed, s_famY, s_U0, s_U1, s_broken;
+    __shared__ int s_armed[2];
+
+    const DevGeom &g = a.g;
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = lane + 32 * warp;
+    const int cb = blockIdx.x, s = blockIdx.y, band = blockIdx.z;
+    const int iu = cb * TMA_COLS + warp;
+    const int iv = band * K1_ROWS + lane;
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    double *partial = MODE != PROJ_STORE ? a.partials + blk : nullptr;
+
+    // family of every column of the block; two families -> plain global path
+    if (lane == 0) {
+        int fam = -1;
+        if (iu < g.nu) fam = g.colB[(size_t)a.views[s] * g.nu + iu].z != 0.f ? 1 : 0;
+        colfam[warp] = fam;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int f = -1, mixed = 0;
+        for (int q = 0; q < TMA_COLS; ++q) {
+            if (colfam[q] < 0) continue;
+            if (f < 0) f = colfam[q];
+            else if (f != colfam[q]) mixed = 1;
+        }
+        s_mixed = mixed || f < 0;
+        s_famY = f;
+    }
+    __syncthreads();
+    if (s_mixed) {  // the masked loop: the same sums as the brick path
+        k1_tile<TX, TB, TO, MODE, TMA_COLS, false>(a, cb, s, band, partial);
+        return;
+    }
+    const bool famY = s_famY == 1;
+    const int Na = famY ? g.ny : g.nx, Nb = famY ? g.nx : g.ny;
+    const ZLayout &L = a.L;
+    const int ps = L.plane_stride(famY), bs = L.inplane_stride(famY);
+    const int base = L.PL + ps + bs;
+    const TX *vol = (const TX *)a.vol;
+
+    RayConst rc;
+    int m0 = 1, m1 = 0;
+    bool has = false;
+    float4 cB = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (iu < g.nu) {
+        const size_t col = (size_t)a.views[s] * g.nu + iu;
+        const float4 cA = g.colA[col];
+        cB = g.colB[col];
+        const FxCol cF = g.colF[col];
+        make_ray<TX>(g, cA, cF, Nb, iv, rc);
+        if (iv < g.nv) plane_range(rc, Na, m0, m1);
+        has = m0 <= m1;
+        if (lane == 0) {  // the band's extreme valid rows of this column
+            const int iv_hi = min(band * K1_ROWS + K1_ROWS - 1, g.nv - 1);
+            const long long n_lo = 2LL * (band * K1_ROWS) - (g.nv - 1), n_hi = 2LL * iv_hi - (g.nv - 1);
+            colz[warp][0] = n_lo * cF.h0 + g.cz_fx;
+            colz[warp][1] = n_lo * cF.h1;
+            colz[warp][2] = n_hi * cF.h0 + g.cz_fx;
+            colz[warp][3] = n_hi * cF.h1;
+            colb[warp][0] = cF.qb0;
+            colb[warp][1] = cF.qb1;
+        }
+    }
+    constexpr int BIG = 1 << 30;
+    const int u0 = __reduce_min_sync(0xffffffffu, has ? m0 : BIG);
+    const int u1 = __reduce_max_sync(0xffffffffu, has ? m1 : -1);
+    if (lane == 0) {
+        s_u0[warp] = u0;
+        s_u1[warp] = u1;
+    }
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_broken = 0;
+        s_armed[0] = s_armed[1] = -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int U0 = BIG, U1 = -1;
+        for (int q = 0; q < TMA_COLS; ++q) {
+            U0 = min(U0, s_u0[q]);
+            U1 = max(U1, s_u1[q]);
+        }
+        s_U0 = U0;
+        s_U1 = U1;
+    }
+    __syncthreads();
+    const int U0 = s_U0, U1 = s_U1;
+    const int nch = U1 >= U0 ? (U1 - U0 + P) / P : 0;
+    const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
+
+    // produce chunk c into buffer c & 1 (one warp; lanes 0..7 take a column each)
+    auto produce = [&](int c) {
+        const int q = c & 1;
+        const int mc = U0 + c * P, me = min(mc + P - 1, U1);
+        long long zlo = LLONG_MAX, zhi = LLONG_MIN, blo = LLONG_MAX, bhi = LLONG_MIN;
+        if (lane < TMA_COLS && colfam[lane] >= 0) {
+            const long long *z = colz[lane];
+            const long long za = z[0] + (long long)mc * z[1], zb = z[0] + (long long)me * z[1];
+            const long long zc = z[2] + (long long)mc * z[3], zd = z[2] + (long long)me * z[3];
+            zlo = min(min(za, zb), min(zc, zd));
+            zhi = max(max(za, zb), max(zc, zd));
+            const long long ba = colb[lane][0] + (long long)mc * colb[lane][1];
+            const long long bb = colb[lane][0] + (long long)me * colb[lane][1];
+            blo = min(ba, bb);
+            bhi = max(ba, bb);
+        }
+        // floors, clamped to the footprint range any inside ray can have
+        int klo = zlo == LLONG_MAX ? BIG : max(fx_floor(zlo), -1);
+        int khi = zhi == LLONG_MIN ? -BIG : min(fx_floor(zhi), g.nz - 1);
+        int b_lo = blo == LLONG_MAX ? BIG : max(fx_floor(blo), -1);
+        int b_hi = bhi == LLONG_MIN ? -BIG : min(fx_floor(bhi), Nb - 1);
+        klo = __reduce_min_sync(0xffffffffu, klo);
+        khi = __reduce_max_sync(0xffffffffu, khi);
+        b_lo = __reduce_min_sync(0xffffffffu, b_lo);
+        b_hi = __reduce_max_sync(0xffffffffu, b_hi);
+        if (lane == 0) {
+            const int kal = klo >= BIG ? 0 : (klo & ~(ALIGN - 1));  // 16-byte z origin
+            const bool ok = !s_broken && klo <= khi && b_lo <= b_hi && khi + 1 - kal <= KZ - 1 &&
+                            b_hi + 1 - b_lo <= KB - 1;
+            meta[q] = TmaMeta{kal, b_lo, mc, ok ? 1 : 0};
+            if (ok) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_tx(&full[q], BRICK_BYTES);
+                // coordinates of the layout: (L.PL + k, i + 1, j + 1)
+                if (famY)
+                    tma_load_3d(bricks + q * BRICK, &mapY, L.PL + kal, b_lo + 1, mc + 1, &full[q]);
+                else
+                    tma_load_3d(bricks + q * BRICK, &mapX, L.PL + kal, mc + 1, b_lo + 1, &full[q]);
+                s_armed[q] = (c >> 1) & 1;
+            } else {
+                mbar_arrive(&full[q]);
+            }
+        }
+    };
+
+    if (nch > 0 && warp == 0) produce(0);
+    float s0 = 0.f, s1 = 0.f;
+    for (int c = 0; c < nch; ++c) {
+        __syncthreads();  // chunk c-1 fully read by every warp; meta[c & 1] visible
+        if (c + 1 < nch && warp == ((c + 1) % TMA_COLS)) produce(c + 1);
+        const int q = c & 1;
+        const TmaMeta mt = meta[q];
+        bool ok = mt.ok != 0;
+        // every chunk's phase completes (a plain arrive when no copy was issued),
+        // so the phases are waited in order; once a wait has given up, no more
+        // waits and no brick reads
+        if (s_broken) {
+            ok = false;
+        } else if (!mbar_wait(&full[q], (c >> 1) & 1)) {
+            ok = false;
+            if (lane == 0) {
+                atomicExch(err, (int)FBL_E_TIMEOUT);
+                s_broken = 1;
+            }
+        }
+        if (ok && lane == 0 && warp == 0) s_armed[q] = -1;
+        const int pa = max(mt.mc, u0), pb = min(mt.mc + P - 1, u1);
+        if (iu >= g.nu || pa > pb) continue;
+        const TX *br = bricks + q * BRICK;
+        const int bstride = famY ? KZ : P * KZ;
+        long long qb = rc.qb0 + (long long)pa * rc.qb1;
+        long long qz = rc.qz0 + (long long)pa * rc.qz1;
+        for (int m = pa; m <= pb; ++m) {
+            const int b0 = fx_floor(qb);
+            const float fb = fx_frac(qb);
+            const int k0 = fx_floor(qz);
+            const float fz = fx_frac(qz);
+            float val = 0.f;
+            if (m >= o0 && m <= o1) {
+                float v00, v10, v01, v11;
+                const int kk = k0 - mt.klo, bb = b0 - mt.blo, mm = m - mt.mc;
+                if (ok && (unsigned)kk <= (unsigned)(KZ - 2) && (unsigned)bb <= (unsigned)(KB - 2)) {
+                    const int idx = (famY ? (mm * KB + bb) * KZ : (bb * P + mm) * KZ) + kk;
+                    v00 = to_f32(br[idx]);
+                    v10 = to_f32(br[idx + 1]);
+                    v01 = to_f32(br[idx + bstride]);
+                    v11 = to_f32(br[idx + bstride + 1]);
+                } else {
+                    const TX *p = vol + (base + m * ps + b0 * bs + k0);
+                    v00 = ldg_f32(p);
+                    v10 = ldg_f32(p + 1);
+                    v01 = ldg_f32(p + bs);
+                    v11 = ldg_f32(p + bs + 1);
+                }
+                const float lo = fmaf(fb, v01 - v00, v00);
+                const float hi = fmaf(fb, v11 - v10, v10);
+                val = fmaf(fz, hi - lo, lo);
+            }
+            if (m & 1) s1 += val; else s0 += val;
+            qb += rc.qb1;
+            qz += rc.qz1;
+        }
+    }
+    // drain: every copy this block issued has landed before shared memory is released
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q)
+            if (s_armed[q] >= 0 && !mbar_wait(&full[q], (unsigned)s_armed[q])) atomicExch(err, (int)FBL_E_TIMEOUT);
+    }
+    float r2 = 0.f;
+    if (iu < g.nu && iv < g.nv) epilogue<TX, TB, TO, MODE>(a, cB, s, iu, iv, rc.w, s0 + s1, r2);
+    if (MODE != PROJ_STORE) {
+        float vv[1] = {r2};
+        double out[1];
+        block_sum_f64<32 * TMA_COLS, 1>(vv, out);
+        if (tid == 0) *partial = out[0];
+    }
+}
+
 // Persistent batched projector: tiles of all volumes (the blocks of
 // k1_project, volume by volume) taken from an atomic counter.  MODE NORM
 // covers only this trial round's searching volumes.  Registers are capped at
@@ -321,8 +626,56 @@ __global__ void __launch_bounds__(256) k_weight(const DevGeom g, const TY *__res
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// Tensor map of the library volume layout [ny+2][nx+2][pitch] with a brick box
+// (KZ, b1, b2) over (k, i, j).
+template <typename TX>
+static bool encode_volume_map(CUtensorMap *map, const void *vol, const ZLayout &L, int b1, int b2) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = sizeof(TX) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (std::is_same<TX, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.nx + 2), (cuuint64_t)(L.ny + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * sizeof(TX),
+                                   (cuuint64_t)L.pitch * (L.nx + 2) * sizeof(TX)};
+    const cuuint32_t box[3] = {(cuuint32_t)TmaShape<TX>::KZ, (cuuint32_t)b1, (cuuint32_t)b2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, dt, 3, const_cast<void *>(vol), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename TX, typename TB, typename TO, int MODE>
+cudaError_t launch_tma(const ProjArgs &a, int n_sel, cudaStream_t st) {
+    alignas(64) CUtensorMap mapX, mapY;
+    // x-plane rays: planes along i, in-plane rows along j; y-plane rays the other way
+    if (!encode_volume_map<TX>(&mapX, a.vol, a.L, TMA_P, TMA_KB) ||
+        !encode_volume_map<TX>(&mapY, a.vol, a.L, TMA_KB, TMA_P))
+        return cudaErrorNotSupported;
+    dim3 block(32, TMA_COLS);
+    dim3 grid((a.g.nu + TMA_COLS - 1) / TMA_COLS, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
+    const size_t smem = 2 * (size_t)TmaShape<TX>::BRICK * sizeof(TX) + 128;
+    k1_project_tma<TX, TB, TO, MODE><<<grid, block, smem, st>>>(a, mapX, mapY, a.g.err);
+    return cudaGetLastError();
+}
+
 template <typename TX, typename TB, typename TO, int MODE>
 cudaError_t launch_t(const ProjArgs &a, int n_sel, cudaStream_t st) {
+    if (a.g.k1_split == 2 && a.g.err) return launch_tma<TX, TB, TO, MODE>(a, n_sel, st);
     const int cols = a.g.k1_cols == 4 ? 4 : 8;
     dim3 block(32, cols);
     dim3 grid((a.g.nu + cols - 1) / cols, n_sel, (a.g.nv + K1_ROWS - 1) / K1_ROWS);
@@ -361,7 +714,7 @@ cudaError_t launch_bdt(int mode, int b_dtype, int out_dtype, const ProjArgs &a, 
 }  // namespace
 
 int project_num_partials(const DevGeom &g, int n_sel) {
-    const int cols = g.k1_cols == 4 ? 4 : 8;
+    const int cols = (g.k1_split == 2 && g.err) ? TMA_COLS : (g.k1_cols == 4 ? 4 : 8);
     return ((g.nu + cols - 1) / cols) * n_sel * ((g.nv + K1_ROWS - 1) / K1_ROWS);
 }
 

@@ -14,7 +14,7 @@ from gpu_common import GEOMS, cuda, host, problem, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cols,split,vpl", list(itertools.product((4, 8), (0, 1), (2, 4, 8, 16))))
+@pytest.mark.parametrize("cols,split,vpl", list(itertools.product((4, 8), (0, 1, 2), (2, 4, 8, 16))))
 def test_every_launch_configuration_matches_oracle(cols, split, vpl):
     import paper_2605_12085_gb300 as fbl
     g = GEOMS["ragged"]
@@ -43,7 +43,7 @@ def test_autotuned_solver_takes_the_same_steps():
     bd = cuda(b.astype(np.float32))
     G = fbl.geometry_create(g)
     rep = fbl.geometry_autotune(G, n_sel=6)
-    assert rep["k1_cols"] in (4, 8) and rep["k2_vpl"] in (2, 4, 8, 16)
+    assert rep["k1_cols"] in (4, 8) and rep["k1_split"] in (0, 1, 2) and rep["k2_vpl"] in (2, 4, 8, 16)
     assert all(t > 0 for t in rep["k1_ms"]) and all(t > 0 for t in rep["k2_ms"])
     runs = []
     for tune in (0, 1):
