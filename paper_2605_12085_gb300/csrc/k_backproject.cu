@@ -22,7 +22,8 @@
 // wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  A column whose rows
 // are spaced by `step` voxels reaches a voxel with at most
 // floor(2 / step * (1 + 1e-4) + 0.002) + 1 rows; columns that need fewer than
-// the geometry's ntap take a loop one tap shorter (a warp-uniform branch).  The residual arrives transposed and zero-padded
+// the geometry's ntap take a loop one tap shorter, and columns whose windows
+// all stay inside the zero pads skip the clamp (warp-uniform branches).  The residual arrives transposed and zero-padded
 // (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
 // lanes' row reads are contiguous and need no bounds test.  The gradient is
 // written in z-innermost order [j][i][k], coalesced.
@@ -51,27 +52,49 @@ struct BpArgs {
 
 // The taps of one candidate column for the lane's VPL voxels: window of NT
 // rows from `lo`, whose first crossing lies d0 voxels from the lane's first
-// voxel (-1 < d0 <= -1 + step).
-template <int NT, int VPL>
+// voxel (-1 < d0 <= -1 + step).  After each voxel the window drops the rows
+// that fell below the next voxel's footprint.  CLAMP: keep each window inside
+// the zero pads (needed only when a lane's windows could leave them; a window
+// clamped into the pads holds no real row since ntap <= RT_PAD).
+template <int NT, int VPL, bool CLAMP>
 __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
                                             int lo, float d0, float step, int lo_max) {
+    const float *r = rcol + lo;
 #pragma unroll
     for (int q = 0; q < VPL; ++q) {
-        // a window clamped into the zero pads holds no real row (ntap <= RT_PAD)
-        const float *r = rcol + min(max(lo, -RT_PAD), lo_max);
+        const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
         float sz = 0.f;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const float d = fmaf((float)t, step, d0);
-            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(r + t), sz);
+            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(w + t), sz);
         }
         acc[q] = fmaf(wb, sz, acc[q]);
         // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
         d0 -= 1.f;
         while (d0 <= -1.f) {
-            ++lo;
+            if (CLAMP) ++lo;
+            else ++r;
             d0 += step;
         }
+    }
+}
+
+// Taps of one column: the tap count (the geometry's, or one fewer when this
+// column's rows are spaced widely enough) and the clamp-free form when every
+// lane's windows stay inside the pads (a warp vote; all lanes are active).
+template <int NTAP, int VPL>
+__device__ __forceinline__ void column_taps_any(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
+                                                int lo, float d0, float step, float inv, int lo_max) {
+    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
+    const bool fewer = NTAP > 1 && (int)(2.f * inv * 1.0001f + 0.002f) + 1 < NTAP;
+    const bool inside = lo >= -RT_PAD && lo + (int)((float)VPL * inv) + 2 <= lo_max;
+    if (__all_sync(0xffffffffu, inside)) {
+        if (fewer) column_taps<NT1, VPL, false>(acc, wb, rcol, lo, d0, step, lo_max);
+        else column_taps<NTAP, VPL, false>(acc, wb, rcol, lo, d0, step, lo_max);
+    } else {
+        if (fewer) column_taps<NT1, VPL, true>(acc, wb, rcol, lo, d0, step, lo_max);
+        else column_taps<NTAP, VPL, true>(acc, wb, rcol, lo, d0, step, lo_max);
     }
 }
 
@@ -132,10 +155,7 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
                 d0 -= step;
             }
             const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
-            if (NTAP > 1 && (int)(2.f * inv * 1.0001f + 0.002f) + 1 < NTAP)
-                column_taps<(NTAP > 1 ? NTAP - 1 : 1), K2_VPL>(acc, wb, rcol, lo, d0, step, lo_max);
-            else
-                column_taps<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, lo_max);
+            column_taps_any<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, inv, lo_max);
         }
     }
     float g2 = 0.f;
