@@ -62,6 +62,8 @@ def parse():
                     help="epochs of plain FP32 that define F* (0: skip time-to-objective)")
     ap.add_argument("--tto-check", type=int, default=3, help="iterations between F evaluations")
     ap.add_argument("--batched", type=int, default=1, help="also time the 16-volume batched launch")
+    ap.add_argument("--launch", default=None,
+                    help="k1_cols,k1_split,k2_vpl for the timed FP32 run instead of the autotuned ones")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     return ap.parse_args()
@@ -458,6 +460,19 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
     return out
 
 
+def aggregate_ranks(ms, units, dist=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' units (host-side reduction over the process group, gloo)."""
+    if dist is None:
+        return float(ms), float(units)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -470,6 +485,10 @@ def run_ours(args, rank, world, local_rank):
     g = wl.geom
     G, xt, b = make_data(fbl, wl, device)
     tune = fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    if args.launch:
+        cols, split, vpl = (int(v) for v in args.launch.split(","))
+        fbl.geometry_set_launch(G, cols, split, vpl)
+        tune = dict(tune, forced={"k1_cols": cols, "k1_split": split, "k2_vpl": vpl})
     params = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
                                 max_backtracks=60)
     S = fbl.fblisa_create(G, params)
@@ -499,13 +518,7 @@ def run_ours(args, rank, world, local_rank):
     ms = t0.elapsed_time(t1)
     prof = S.profile(False)
     units = sum(step_units(st, g) for st in stats)
-    ms_max, units_all = ms, units
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([float(units)], dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms_max, units_all = float(t[0]), float(u[0])
+    ms_max, units_all = aggregate_ranks(ms, units, dist)
     value = units_all / (ms_max * 1e-3) / 1e9
 
     # dominant kernel: the trial-objective projection (K1')
