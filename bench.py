@@ -43,8 +43,8 @@ K3_BYTES_PER_VOXEL = 12  # read x and g, write x_bar (FP32)
 # 512^3 / 768^2 / 40-view FP32 workload, from one ncu capture
 # (profiles/dram_traffic_c3_512.md); valid only for the projector source it
 # was taken on, so it is reported only while k_project.cu has that hash.
-K1_TRAFFIC = {"workload": "c3_512", "bytes_per_launch": 11.000e9,
-              "source_sha256": "f47c3b232c1dec7ea3e776bfcc975171501adb8f0ce17932ba28a14a36aca094"}
+K1_TRAFFIC = {"workload": "c3_512", "bytes_per_launch": 10.70e9,
+              "source_sha256": "136c4c66277e84cffa4159b3c72c89d6817f04f0fc72c59e5eb7476cdee14685"}
 
 
 def parse():
