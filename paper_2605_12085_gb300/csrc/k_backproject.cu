@@ -22,8 +22,8 @@
 // wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  A column whose rows
 // are spaced by `step` voxels reaches a voxel with at most
 // floor(2 / step * (1 + 1e-4) + 0.002) + 1 rows; columns that need fewer than
-// the geometry's ntap take a loop one tap shorter, and columns whose windows
-// all stay inside the zero pads skip the clamp (warp-uniform branches).  The residual arrives transposed and zero-padded
+// the geometry's ntap take a loop one or two taps shorter, and columns whose
+// windows all stay inside the zero pads skip the clamp (warp-uniform branches).  The residual arrives transposed and zero-padded
 // (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
 // lanes' row reads are contiguous and need no bounds test.  The gradient is
 // written in z-innermost order [j][i][k], coalesced.
@@ -80,22 +80,31 @@ __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const f
     }
 }
 
-// Taps of one column: the tap count (the geometry's, or one fewer when this
-// column's rows are spaced widely enough) and the clamp-free form when every
-// lane's windows stay inside the pads (a warp vote; all lanes are active).
+// Taps of one column: this column's own tap count floor(2 inv) + 1 (the
+// geometry's NTAP, or one or two fewer: rows spaced wider than the geometry's
+// closest), and the clamp-free form when every lane's windows stay inside the
+// pads (a warp vote; all lanes are active).  A window with more taps than
+// needed gives the same sums (the extra taps weigh exactly 0).
+template <int NTAP, int VPL, bool CLAMP>
+__device__ __forceinline__ void column_taps_nt(int nt, float (&acc)[VPL], float wb,
+                                               const float *__restrict__ rcol, int lo, float d0, float step,
+                                               int lo_max) {
+    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
+    constexpr int NT2 = NTAP > 2 ? NTAP - 2 : NT1;
+    if (nt <= NT2) column_taps<NT2, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+    else if (nt <= NT1) column_taps<NT1, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+    else column_taps<NTAP, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+}
+
 template <int NTAP, int VPL>
 __device__ __forceinline__ void column_taps_any(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
                                                 int lo, float d0, float step, float inv, int lo_max) {
-    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
-    const bool fewer = NTAP > 1 && (int)(2.f * inv * 1.0001f + 0.002f) + 1 < NTAP;
+    const int nt = (int)(2.f * inv * 1.0001f + 0.002f) + 1;
     const bool inside = lo >= -RT_PAD && lo + (int)((float)VPL * inv) + 2 <= lo_max;
-    if (__all_sync(0xffffffffu, inside)) {
-        if (fewer) column_taps<NT1, VPL, false>(acc, wb, rcol, lo, d0, step, lo_max);
-        else column_taps<NTAP, VPL, false>(acc, wb, rcol, lo, d0, step, lo_max);
-    } else {
-        if (fewer) column_taps<NT1, VPL, true>(acc, wb, rcol, lo, d0, step, lo_max);
-        else column_taps<NTAP, VPL, true>(acc, wb, rcol, lo, d0, step, lo_max);
-    }
+    if (__all_sync(0xffffffffu, inside))
+        column_taps_nt<NTAP, VPL, false>(nt, acc, wb, rcol, lo, d0, step, lo_max);
+    else
+        column_taps_nt<NTAP, VPL, true>(nt, acc, wb, rcol, lo, d0, step, lo_max);
 }
 
 // One block's work: voxel columns i = bx*8 .. bx*8+7 of row j, z-span bz;
