@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--batched", type=int, default=1, help="also time the 16-volume batched launch")
     ap.add_argument("--launch", default=None,
                     help="k1_cols,k1_split,k2_vpl for the timed FP32 run instead of the autotuned ones")
+    ap.add_argument("--comparators", type=int, default=0,
+                    help="also run the paper's comparison: FB, full-batch and mini-batch FB-LISA (2+ min)")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     return ap.parse_args()
@@ -232,6 +234,86 @@ def c5b_record(fbl, device, steps=5, warmup=2):
             del bv
         torch.cuda.empty_cache()
     del b, G
+    torch.cuda.empty_cache()
+    return out
+
+
+def comparators_record(fbl, device, budget_s=30.0):
+    """The paper's comparison (Sec. 3) on the 512^3 workload, each method for a
+    fixed budget of GPU time (sum of CUDA-event step times; F and RE are
+    evaluated off the clock): deterministic forward-backward (full batch,
+    constant step 0.9/L, L = ||A||^2 by power iteration), FB-LISA with the full
+    batch, FB-LISA with 40-view mini-batches (plain FP32), and the fast
+    configuration (learned proposal + BF16 + graph)."""
+    import torch
+    import synth
+    from paper_2605_12085_gb300 import proposal as prop
+    wl = synth.WORKLOADS["c3_512"]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    xt_d = torch.from_numpy(xt).to(device)
+    stream = torch.cuda.current_stream(device)
+    views = list(range(g.n_views))
+    # L by power iteration on A^T A over all views
+    v = torch.ones(g.vol_shape, dtype=torch.float32, device=device)
+    y = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
+    lam = 0.0
+    for _ in range(12):
+        fbl.project(G, v, views, y=y)
+        w = fbl.backproject(G, y, views)
+        lam = float(torch.linalg.vector_norm(w) / torch.linalg.vector_norm(v))
+        v = w / torch.linalg.vector_norm(w)
+    del y, v, w
+    L = lam * 1.02
+    net, _ = prop.load()
+    b16 = b.to(torch.bfloat16)
+
+    def run(params, fast=False, check_every=1):
+        S = fbl.fblisa_create(G, params)
+        if fast:
+            S.set_proposal(net, margin=0.25)
+        x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32, device=device)
+        bb = b16 if fast else b
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el, k, hist = 0.0, 0, []
+        F0, _, re0 = fbl.evaluate(G, x.float(), b, wl.mu, x_true=xt_d)
+        hist.append((0.0, 0, F0, re0))
+        while el < budget_s and k < 2000:
+            e0.record(stream)
+            S.step(x, bb)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            el += e0.elapsed_time(e1) * 1e-3
+            k += 1
+            if k % check_every == 0:
+                F, _, re = fbl.evaluate(G, x.float(), b, wl.mu, x_true=xt_d)
+                hist.append((el, k, F, re))
+        return hist
+
+    base = dict(beta=0.5, mu=wl.mu, seed=wl.seed_batches)
+    runs = {
+        "fb_fixed_full_batch": run(fbl.params_default(alpha0=0.9 / L, N0=g.n_views, fixed_step=1, **base)),
+        "fblisa_full_batch": run(fbl.params_default(alpha0=1e-3, N0=g.n_views, **base)),
+        "fblisa_minibatch_fp32": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, **base), check_every=5),
+        "fblisa_fast": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, x_dtype=fbl.BF16, b_dtype=fbl.BF16,
+                                              use_graph=1, proposal=1, **base), fast=True, check_every=5),
+    }
+    # target: the mini-batch FP32 method's objective after 10 epochs (180 iterations)
+    mb = runs["fblisa_minibatch_fp32"]
+    F_star = next((h[2] for h in mb if h[1] >= 180), mb[-1][2])
+    out = {"workload": "c3_512", "budget_s_per_method": budget_s, "L_estimate": L,
+           "fb_step": 0.9 / L, "F_star_minibatch_10_epochs": F_star}
+    for name, h in runs.items():
+        at = {}
+        for t in (5.0, 10.0, 20.0, budget_s):
+            last = [r for r in h if r[0] <= t]
+            at["%gs" % t] = {"F": last[-1][2], "rel_error": last[-1][3], "iterations": last[-1][1]}
+        hit = next((r for r in h if r[2] <= F_star * (1 + 1e-3)), None)
+        out[name] = {"at": at, "time_to_F_star_1e-3_s": hit[0] if hit else None,
+                     "iterations_run": h[-1][1], "final_F": h[-1][2], "final_rel_error": h[-1][3]}
+    del G, b, b16, xt_d
     torch.cuda.empty_cache()
     return out
 
@@ -603,6 +685,9 @@ def run_ours(args, rank, world, local_rank):
 
     if args.c5b and rank == 0:
         out["c5b"] = c5b_record(fbl, device)
+
+    if args.comparators and rank == 0:
+        out["comparators"] = comparators_record(fbl, device)
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,

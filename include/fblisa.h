@@ -105,6 +105,11 @@ typedef struct {
                                  whose WHILE node repeats the trial until (2.3) holds */
     int32_t force_reject;     /* test hook: every trial fails (2.3) */
     int32_t autotune;         /* 1: time the kernels' launch configurations at creation */
+    int32_t fixed_step;       /* 1: forward-backward with the constant step alpha0 and no line
+                                 search (the deterministic FB baseline of Sec. 3 when
+                                 N0 = n_max = n_views): no trial objective is evaluated,
+                                 f_xbar and margin are reported as NaN; use_graph and
+                                 proposal are ignored */
 } fbl_params;
 
 /* Record of one iteration of Algorithm 1. */
@@ -129,7 +134,8 @@ typedef struct {
 } fbl_step_stats;
 
 /* Defaults: alpha0 1e-3, beta 0.5, mu 1, C 1, eps_base 0.99, N0 8, n_max 0,
- * max_backtracks 60, proposal 0, seed 0, F32 storage, no graph, no hook. */
+ * max_backtracks 60, proposal 0, seed 0, F32 storage, no graph, no hook,
+ * no autotuning, line search on (fixed_step 0). */
 FBL_API void fbl_params_default(fbl_params *p);
 
 /*

@@ -113,6 +113,7 @@ class Params:
     n_max: int = 0            # 0 -> n_theta
     max_backtracks: int = 60
     seed: int = 0
+    fixed_step: bool = False  # forward-backward with the constant step alpha0, no test (2.3)
 
 
 @dataclasses.dataclass
@@ -169,6 +170,14 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
     alpha = p.alpha0 if alpha_init is None else alpha_init
     if replay_alpha is not None:
         alpha = replay_alpha
+    if p.fixed_step:
+        # the deterministic FB baseline of Sec. 3 (with the full batch): one
+        # forward-backward step at the constant alpha_0, no sufficient-decrease test
+        xbar = prox(x - p.alpha0 * g, p.alpha0, p.mu)
+        d = xbar - x
+        t = Trial(p.alpha0, float("nan"), float(np.dot(g.ravel(), d.ravel())),
+                  float(np.dot(d.ravel(), d.ravel())), float("nan"), float("nan"), True)
+        return xbar, StepRecord(k, epoch, N_t, list(views), rho0, f_x, [t], p.alpha0, 0)
     trials = []
     for bt in range(p.max_backtracks + 1):
         # Step 2c: forward-backward point and the test (2.3)

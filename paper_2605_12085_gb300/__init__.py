@@ -44,7 +44,8 @@ class fbl_params(ctypes.Structure):
                 ("max_backtracks", ctypes.c_int32), ("proposal", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("x_dtype", ctypes.c_int32),
                 ("b_dtype", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("force_reject", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("force_reject", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("fixed_step", ctypes.c_int32)]
 
 
 class fbl_step_stats(ctypes.Structure):

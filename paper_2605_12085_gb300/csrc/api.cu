@@ -999,6 +999,65 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     }
     const int xdt = s->p.x_dtype;
     const double scale = (double)d.n_views / (double)N;
+    if (s->p.fixed_step) {
+        // forward-backward with the constant step alpha0 and no test of (2.3)
+        int np = 0, npp = 0;
+        CK(prof_launch(s, 0, st, [&] {
+               return launch_project(PROJ_RESID, s->dg, s->st, s->L, xdt, s->d_views, N, bd, s->p.b_dtype,
+                                     bmap, s->rt, FBL_F32, s->partials, &np, st);
+           }),
+           "residual kernel");
+        CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
+           "reduce");
+        CK(prof_launch(s, 2, st, [&] {
+               return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials);
+           }),
+           "gradient kernel");
+        const int nbp = backproject_num_partials(s->dg);
+        CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, nbp, nbp, 1, s->d_sc + 5, st); }),
+           "reduce");
+        const double alpha = s->p.alpha0;
+        CK(prof_launch(s, 3, st, [&] {
+               return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu), s->tr, xdt,
+                                     s->partials, &npp, st);
+           }),
+           "prox kernel");
+        CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
+           "reduce");
+        CK(cudaMemcpyAsync(s->h_sc, s->d_sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+        CK(cudaStreamSynchronize(st), "fixed step");
+        prof_flush(s);
+        const double f_x = 0.5 * scale * s->h_sc[0];
+        if (!std::isfinite(f_x) || !std::isfinite(s->h_sc[2])) {
+            restore();
+            return fail(FBL_E_NONFINITE, "fblisa_step: non-finite objective or reduction at k=%lld",
+                        (long long)s->k);
+        }
+        if (check_timeout(g, s->dg, st)) {
+            restore();
+            return fail(FBL_E_TIMEOUT, "fblisa_step: a bounded wait of the projector gave up");
+        }
+        if (stats) {
+            std::memset(stats, 0, sizeof *stats);
+            stats->k = s->k;
+            stats->epoch = s->epoch;
+            stats->N_t = N;
+            stats->alpha = alpha;
+            stats->alpha_init = alpha;
+            stats->rho0 = s->h_sc[0];
+            stats->f_x = f_x;
+            stats->f_xbar = std::nan("");
+            stats->gTd = s->h_sc[1];
+            stats->dnorm2 = s->h_sc[2];
+            stats->margin = std::nan("");
+            stats->grad_norm2 = s->h_sc[5];
+            stats->status = FBL_OK;
+        }
+        std::swap(s->st, s->tr);
+        s->k += 1;
+        s->iter_in_epoch += 1;
+        return FBL_OK;
+    }
     if (s->p.use_graph) {
         // the whole iteration, backtracking included, as one graph launch
         fbl_solver::GraphEntry *ge = nullptr;
@@ -1445,6 +1504,7 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     if (p->N0 < 1 || p->N0 > n_max || n_max > d.n_views)
         return fail(FBL_E_INVAL, "fblisa_create: need 1 <= N0 <= n_max <= n_views");
     if (p->proposal != 0 && p->proposal != 1) return fail(FBL_E_INVAL, "fblisa_create: proposal must be 0 or 1");
+    if (p->fixed_step != 0 && p->fixed_step != 1) return fail(FBL_E_INVAL, "fblisa_create: fixed_step must be 0 or 1");
     auto s = new fbl_solver();
     s->g = g;
     s->dg = g->dg;
@@ -1908,6 +1968,8 @@ extern "C" fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, cons
         if (geoms[v]->device != dev) return fail(FBL_E_INVAL, "fblisa_batch_create: geometries on different devices");
         if (params[v].x_dtype != params[0].x_dtype || params[v].b_dtype != params[0].b_dtype)
             return fail(FBL_E_INVAL, "fblisa_batch_create: every volume needs the same x_dtype and b_dtype");
+        if (params[v].fixed_step)
+            return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: the batch runs the line search (fixed_step 0)");
     }
     if (params[0].b_dtype != params[0].x_dtype)
         return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: b_dtype must equal x_dtype");

@@ -225,3 +225,35 @@ def test_splitmix64_stream_properties():
     assert len(set(zs)) == len(zs)
     bits = np.array([[(z >> s) & 1 for s in range(0, 64, 7)] for z in zs])
     assert np.all(np.abs(bits.mean(axis=0) - 0.5) < 0.04)
+
+
+def test_fixed_step_forward_backward_descent_lemma():
+    # Constant-step FB on the full batch with alpha <= 1/L: the descent lemma and
+    # the prox optimality give F(x+) <= F(x) - ||x+ - x||^2 / (2 alpha) (textbook
+    # proximal gradient), so F decreases; a gradient of the wrong sign or a
+    # missing prox shift breaks it.  Past 2/L the iteration diverges.
+    g, xt, b = _problem(8)
+    views = list(range(g.n_views))
+    L = _lipschitz(g, views)
+    x = np.zeros(g.vol_shape)
+    p = fblisa.Params(alpha0=0.9 / L, mu=0.1, N0=g.n_views, fixed_step=True)
+    F = fblisa.full_objective(g, x, b, p.mu)
+    for _ in range(15):
+        xn, rec = fblisa.fb_step(g, x, b, views, p)
+        Fn = fblisa.full_objective(g, xn, b, p.mu)
+        d2 = float(((xn - x) ** 2).sum())
+        assert rec.backtracks == 0 and rec.alpha == p.alpha0
+        assert Fn <= F - d2 / (2 * p.alpha0) + 1e-10 * abs(F)
+        x, F = xn, Fn
+    assert F < 0.5 * fblisa.full_objective(g, np.zeros(g.vol_shape), b, p.mu)
+    # same point as the line search's first trial at the same step
+    x0 = np.full(g.vol_shape, 0.2)
+    a, _ = fblisa.fb_step(g, x0, b, views, p)
+    c, _ = fblisa.fb_step(g, x0, b, views, fblisa.Params(alpha0=0.9 / L, mu=0.1, N0=g.n_views))
+    assert np.array_equal(a, c)
+    # far beyond 2/L the constant step does not converge
+    q = fblisa.Params(alpha0=5.0 / L, mu=0.0, N0=g.n_views, fixed_step=True)
+    y = np.full(g.vol_shape, 0.3)
+    for _ in range(6):
+        y, _ = fblisa.fb_step(g, y, b, views, q)
+    assert fblisa.full_objective(g, y, b, 0.0) > fblisa.full_objective(g, np.full(g.vol_shape, 0.3), b, 0.0)
