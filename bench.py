@@ -66,6 +66,8 @@ def parse():
                     help="k1_cols,k1_split,k2_vpl for the timed FP32 run instead of the autotuned ones")
     ap.add_argument("--comparators", type=int, default=0,
                     help="also run the paper's comparison: FB, full-batch and mini-batch FB-LISA (2+ min)")
+    ap.add_argument("--paper-cases", type=int, default=0,
+                    help="also run the paper-shaped 560^3 cases with RE / PSNR over time (several minutes)")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     return ap.parse_args()
@@ -315,6 +317,94 @@ def comparators_record(fbl, device, budget_s=30.0):
                      "iterations_run": h[-1][1], "final_F": h[-1][2], "final_rel_error": h[-1][3]}
     del G, b, b16, xt_d
     torch.cuda.empty_cache()
+    return out
+
+
+def paper_cases_record(fbl, device, budget_s=30.0):
+    """The paper's three cases (Sec. 3) in shape on seeded phantoms (the walnut
+    data are not available): 560^3, 36 / 36 / 72 views, 840^2 detector,
+    N_0 = 8, alpha_0 = 1e-3, mu = 2 / 1 / 1.  Each method runs for budget_s of
+    GPU time: plain FB-LISA (FP32), the fast configuration, and constant-step
+    FB on the full batch (step 0.9/L).  Reported: RE = ||x - x_true|| /
+    ||x_true|| and PSNR = 10 log10(max(x_true)^2 / MSE) at fixed times and at
+    iterations 120 and 240 (the paper's 120 s / 240 s budgets ran at about one
+    iteration per second), and the best RE seen."""
+    import math
+    import torch
+    import synth
+    from paper_2605_12085_gb300 import proposal as prop
+    net, _ = prop.load()
+    stream = torch.cuda.current_stream(device)
+    out = {"budget_s_per_method": budget_s}
+    for case in ("case1_560", "case2_560", "case3_560"):
+        wl = synth.WORKLOADS[case]
+        g = wl.geom
+        G, xt, b = make_data(fbl, wl, device)
+        fbl.geometry_autotune(G, fbl.F32, wl.N0)
+        xt_d = torch.from_numpy(xt).to(device)
+        peak2 = float(xt.max()) ** 2
+        xt_n2 = float((xt.astype("float64") ** 2).sum())
+        views = list(range(g.n_views))
+        v = torch.ones(g.vol_shape, dtype=torch.float32, device=device)
+        lam = 0.0
+        for _ in range(12):
+            w = fbl.backproject(G, fbl.project(G, v, views), views)
+            lam = float(torch.linalg.vector_norm(w) / torch.linalg.vector_norm(v))
+            v = w / torch.linalg.vector_norm(w)
+        del v, w
+        L = lam * 1.02
+        b16 = b.to(torch.bfloat16)
+
+        def psnr(re):
+            mse = re * re * xt_n2 / g.n_vox
+            return 10.0 * math.log10(peak2 / mse) if mse > 0 else float("inf")
+
+        def run(params, fast=False):
+            S = fbl.fblisa_create(G, params)
+            if fast:
+                S.set_proposal(net, margin=0.25)
+            x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32, device=device)
+            bb = b16 if fast else b
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            el, k, hist = 0.0, 0, []
+            while el < budget_s and k < 5000:
+                e0.record(stream)
+                S.step(x, bb)
+                e1.record(stream)
+                torch.cuda.synchronize(device)
+                el += e0.elapsed_time(e1) * 1e-3
+                k += 1
+                if k % 10 == 0 or k in (120, 240):
+                    F, _, re = fbl.evaluate(G, x.float(), b, wl.mu, x_true=xt_d)
+                    hist.append((el, k, F, re))
+            rec = {"iterations": k, "ms_per_iteration": 1e3 * el / max(k, 1)}
+            for t in (budget_s / 4, budget_s / 2, budget_s):
+                last = [h for h in hist if h[0] <= t]
+                if last:
+                    rec["at_%gs" % t] = {"rel_error": last[-1][3], "psnr_db": psnr(last[-1][3]),
+                                         "F": last[-1][2], "iterations": last[-1][1]}
+            for it in (120, 240):
+                h = next((h for h in hist if h[1] == it), None)
+                if h:
+                    rec["at_iteration_%d" % it] = {"rel_error": h[3], "psnr_db": psnr(h[3]), "F": h[2],
+                                                   "seconds": h[0]}
+            if hist:
+                best = min(hist, key=lambda h: h[3])
+                rec["best"] = {"rel_error": best[3], "psnr_db": psnr(best[3]), "iterations": best[1],
+                               "seconds": best[0]}
+            return rec
+
+        base = dict(beta=0.5, mu=wl.mu, seed=wl.seed_batches)
+        out[case] = {
+            "views": g.n_views, "mu": wl.mu, "noise_rel": wl.noise_rel, "L_estimate": L,
+            "fblisa_fp32": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, **base)),
+            "fblisa_fast": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, x_dtype=fbl.BF16, b_dtype=fbl.BF16,
+                                                  use_graph=1, proposal=1, **base), fast=True),
+            "fb_fixed_full_batch": run(fbl.params_default(alpha0=0.9 / L, N0=g.n_views, fixed_step=1, **base)),
+        }
+        del G, b, b16, xt_d
+        torch.cuda.empty_cache()
     return out
 
 
@@ -688,6 +778,9 @@ def run_ours(args, rank, world, local_rank):
 
     if args.comparators and rank == 0:
         out["comparators"] = comparators_record(fbl, device)
+
+    if args.paper_cases and rank == 0:
+        out["paper_cases"] = paper_cases_record(fbl, device)
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,

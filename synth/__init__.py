@@ -96,6 +96,15 @@ WORKLOADS: Dict[str, Workload] = {
                        N0=20, epochs=20, seed_phantom=1002, seed_noise=2002, seed_batches=3002),
     "c3_512": Workload("c3_512", _cube(512, 720, 768), 100, 0, 0.02, "gaussian", 0.01, 0.0,
                        N0=40, epochs=10, seed_phantom=1003, seed_noise=2003, seed_batches=3003),
+    # the paper's three walnut cases (Sec. 3) in shape only: 560^3, 36 / 36 / 72
+    # views, N_0 = 8, mu = 2 / 1 / 1, case 1 noise-free and cases 2-3 with
+    # Gaussian noise of 2% of the maximum (the paper's "2% variance" read as that)
+    "case1_560": Workload("case1_560", _cube(560, 36, 840), 60, 0, 0.02, "gaussian", 0.0, 0.0,
+                          N0=8, epochs=0, seed_phantom=1301, seed_noise=2301, seed_batches=3301, mu=2.0),
+    "case2_560": Workload("case2_560", _cube(560, 36, 840), 60, 0, 0.02, "gaussian", 0.02, 0.0,
+                          N0=8, epochs=0, seed_phantom=1302, seed_noise=2302, seed_batches=3302, mu=1.0),
+    "case3_560": Workload("case3_560", _cube(560, 72, 840), 60, 0, 0.02, "gaussian", 0.02, 0.0,
+                          N0=8, epochs=0, seed_phantom=1303, seed_noise=2303, seed_batches=3303, mu=1.0),
     # a profiling-sized case: volume larger than L2, a few GB on the device in all
     "p384": Workload("p384", _cube(384, 120, 576), 40, 0, 0.0, "gaussian", 0.01, 0.0,
                      N0=20, epochs=2, seed_phantom=1009, seed_noise=2009, seed_batches=3009),
