@@ -9,7 +9,9 @@ Contents:
   * ``project`` / ``backproject`` / ``project_rays`` / ``backproject_voxels``
     -- the cone-beam operator A_S of eq. (2.5) and its exact transpose, in
     plain C double precision (``joseph.c``);
-  * ``fblisa`` -- Algorithm 1 (FB-LISA) step by step in numpy float64.
+  * ``fblisa`` -- Algorithm 1 (FB-LISA) step by step in numpy float64;
+  * ``fdk`` -- the FDK reconstruction (cosine weighting, Ram-Lak filter,
+    weighted backprojection) in numpy float64.
 
 Pins (checks against facts the paper and mathematics fix, not against this
 code) live in ``tests/test_oracle_*.py``.  One function is "parity unpinned"

@@ -1,0 +1,77 @@
+"""Pins of the FDK oracle against facts that do not come from its code:
+
+* the discrete Ram-Lak kernel is the band-limited ramp: its spectrum
+  t * sum_k h(k t) cos(2 pi f k t) equals |f| on [0, 1/(2t)] up to the tail
+  truncated at the detector width (at most 1/(pi^2 nu t) + a rounding term);
+* the view weights cover the circle once (sum 2 pi), uniform angles give
+  2 pi / n each;
+* a uniform ball reconstructed from its analytic projections (exact chord
+  lengths 2 sqrt(R^2 - d^2), no projector involved) comes out at its value in
+  the interior of the central slice, and 0 well outside it.
+"""
+import math
+
+import numpy as np
+
+from oracle import fdk
+import synth
+
+
+def test_ramp_kernel_spectrum_is_band_limited_ramp():
+    for nu, t in ((64, 1.0), (301, 0.7)):
+        h = fdk.ramp_kernel(nu, t)
+        k = np.arange(-(nu - 1), nu)
+        f = np.linspace(0.0, 0.5 / t, 97)
+        R = t * (h[None, :] * np.cos(2 * math.pi * f[:, None] * k[None, :] * t)).sum(axis=1)
+        assert np.max(np.abs(R - f)) <= 1.0 / (math.pi ** 2 * nu * t) * 1.05 + 1e-12
+        assert h[nu - 1] == 1.0 / (4 * t * t) and h[nu] < 0 and h[nu + 1] == 0.0
+
+
+def test_view_weights_cover_the_circle():
+    w = fdk.view_weights(2 * math.pi * np.arange(12) / 12)
+    assert np.allclose(w, 2 * math.pi / 12)
+    ang = np.array([0.3, 1.0, 2.5, 4.0, 6.0])
+    w = fdk.view_weights(ang)
+    assert math.isclose(w.sum(), 2 * math.pi, rel_tol=1e-12)
+    assert math.isclose(w[1], 0.5 * (2.5 - 0.3))                  # half the gaps to its neighbours
+    assert math.isclose(w[0], 0.5 * (1.0 - (6.0 - 2 * math.pi)))   # across the 0 / 2 pi seam
+
+
+def _ball_projections(g, R, value):
+    """Exact line integrals of a uniform ball (radius R, centred) for every ray."""
+    th = 2 * math.pi * np.arange(g.n_views) / g.n_views
+    cu, cv = (g.nu - 1) / 2.0, (g.nv - 1) / 2.0
+    u = (np.arange(g.nu) - cu) * g.du
+    v = (np.arange(g.nv) - cv) * g.dv
+    y = np.zeros((g.n_views, g.nv, g.nu))
+    for s, a in enumerate(th):
+        c, sn = math.cos(a), math.sin(a)
+        src = np.array([g.sod * c, g.sod * sn, 0.0])
+        det = -(g.sdd - g.sod) * np.array([c, sn, 0.0])
+        eu = np.array([-sn, c, 0.0])
+        P = det[None, None, :] + u[None, :, None] * eu[None, None, :] + v[:, None, None] * np.array([0, 0, 1.0])
+        d = P - src
+        d /= np.linalg.norm(d, axis=-1, keepdims=True)
+        cross = np.cross(-src[None, None, :], d)  # (centre - source) x direction
+        dist2 = (cross ** 2).sum(axis=-1)
+        y[s] = value * 2.0 * np.sqrt(np.maximum(R * R - dist2, 0.0))
+    return y
+
+
+def test_uniform_ball_from_exact_projections():
+    g = synth.Geometry(nx=48, ny=48, nz=9, vx=1.0, vy=1.0, vz=1.0, n_views=180, sod=400.0, sdd=600.0,
+                       nu=96, nv=40, du=1.5, dv=1.5)
+    R, value = 15.0, 1.0
+    y = _ball_projections(g, R, value)
+    f = fdk.fdk(g, y, range(g.n_views))
+    mid = f[g.nz // 2]
+    jj, ii = np.meshgrid(np.arange(g.ny), np.arange(g.nx), indexing="ij")
+    r = np.hypot((ii - (g.nx - 1) / 2.0) * g.vx, (jj - (g.ny - 1) / 2.0) * g.vy)
+    inside = mid[r < 0.7 * R]
+    outside = mid[r > 1.4 * R]
+    assert abs(inside.mean() - value) <= 0.02 * value
+    assert np.max(np.abs(inside - value)) <= 0.06 * value
+    assert np.max(np.abs(outside)) <= 0.03 * value
+    # the sampled-voxel form gives the same values
+    vox = [(g.nz // 2, 24, 24), (g.nz // 2, 10, 30), (0, 5, 5)]
+    assert np.allclose(fdk.fdk(g, y, range(g.n_views), voxels=vox), [f[v] for v in vox], rtol=0, atol=1e-12)
