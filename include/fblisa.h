@@ -196,6 +196,27 @@ FBL_API fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_d
                        void *stream);
 
 /*
+ * fdk -- the FDK reconstruction (Feldkamp-Davis-Kress), the analytic method
+ * the paper compares with and uses to make its reference volumes (Sec. 3,
+ * "Dataset" and the comparison methods), for the circular orbit and flat
+ * detector of g, on the virtual detector through the rotation axis
+ * (m = sod/sdd): cosine weighting sod / sqrt(sod^2 + a^2 + b^2) of each pixel
+ * (a, b = its coordinates times m), Ram-Lak filtering of each detector row
+ * (spatial kernel of spacing t = du m: h(0) = 1/(4 t^2), h(k t) =
+ * -1/(pi^2 k^2 t^2) for odd k, 0 else; zero outside the detector), and the
+ * weighted backprojection sum over views of (dtheta/2) q(eta/U, z/U) / U^2,
+ * U = (sod - xi)/sod, bilinear on the detector and zero outside it; dtheta of
+ * a view is half the circular gaps to its neighbours among the listed views.
+ * y: [n_sel][nv][nu] of y_dtype, the projections of views[] (host int32);
+ * x: [nz][ny][nx] float32, overwritten (zero when n_sel == 0).  Host or device
+ * buffers; the library allocates its scratch (filtered projections of up to
+ * 256 views, one volume).  FP32 filtering and interpolation, detector
+ * coordinates from FP64 per voxel column.
+ */
+FBL_API fbl_status fdk(const fbl_geometry *g, const void *y, int32_t y_dtype, const int32_t *views,
+                       int32_t n_sel, float *x, void *stream);
+
+/*
  * residual_norm -- rho = ||A_N x - b_N||^2 in FP64 (the mini-batch fidelity
  * of eq. (2.5) up to the factor n_theta/(2 N_t)), without storing A_N x.
  * b: the full sinogram [n_views][nv][nu] of b_dtype; the listed views are

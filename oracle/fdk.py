@@ -75,13 +75,21 @@ def filtered(geom, y: np.ndarray, views: Sequence[int]) -> np.ndarray:
     b = (np.arange(geom.nv) - cv) * geom.dv * m
     W = geom.sod / np.sqrt(geom.sod ** 2 + a[None, :] ** 2 + b[:, None] ** 2)
     t = geom.du * m
-    h = ramp_kernel(geom.nu, t)
-    y = np.asarray(y, dtype=np.float64).reshape(len(views), geom.nv, geom.nu)
+    nu = geom.nu
+    h = ramp_kernel(nu, t)  # h(k t), k = -(nu-1) .. nu-1
+    # q_i = t sum_n h(i - n) p_n as a circular convolution of length 2 nu: the
+    # kernel's negative offsets sit at the end of the period, and for outputs
+    # 0 <= i < nu no product wraps onto another (|i - n| <= nu - 1 < nu + 1)
+    L = 2 * nu
+    hc = np.zeros(L)
+    hc[:nu] = h[nu - 1:]            # k = 0 .. nu-1
+    hc[L - (nu - 1):] = h[:nu - 1]  # k = -(nu-1) .. -1
+    Hf = np.fft.rfft(hc)
+    y = np.asarray(y, dtype=np.float64).reshape(len(views), geom.nv, nu)
     q = np.empty_like(y)
     for s in range(len(views)):
         pw = y[s] * W
-        for r in range(geom.nv):
-            q[s, r] = t * np.convolve(pw[r], h)[geom.nu - 1: 2 * geom.nu - 1]
+        q[s] = t * np.fft.irfft(np.fft.rfft(pw, n=L, axis=1) * Hf[None, :], n=L, axis=1)[:, :nu]
     return q
 
 

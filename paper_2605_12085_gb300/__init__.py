@@ -84,7 +84,7 @@ EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_
            "geometry_set_launch", "evaluate", "mlp_forward", "mlp_gradient", "mlp_train",
            "fblisa_set_proposal", "fblisa_batch_create", "fblisa_batch_destroy",
            "fblisa_batch_set_proposal", "fblisa_batch_step", "fblisa_batch_run",
-           "fblisa_batch_info", "fblisa_batch_last_batch"]
+           "fblisa_batch_info", "fblisa_batch_last_batch", "fdk"]
 
 
 def _load():
@@ -123,6 +123,7 @@ def _load():
         "fblisa_batch_run": (st, [vp, P(vp), P(vp), i32, P(fbl_step_stats), i64, P(i64), vp]),
         "fblisa_batch_info": (st, [vp, P(i32), P(i64)]),
         "fblisa_batch_last_batch": (st, [vp, i32, P(i32), i32, P(i32)]),
+        "fdk": (st, [vp, vp, i32, P(i32), i32, vp, vp]),
         "fbl_last_error": (ctypes.c_char_p, []),
         "fbl_schedule": (st, [i32, i32, i32, dbl, dbl, i32, P(i32), P(i32)]),
         "fbl_epoch_batches": (st, [ctypes.c_uint64, i32, i32, i32, P(i32)]),
@@ -278,6 +279,19 @@ def backproject(geom: Geometry, y, views: Sequence[int], x=None, accumulate: boo
     _check(lib.backproject(geom.handle, _ptr(y), _dtype_code(y),
                            v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), v.size, _ptr(x),
                            int(bool(accumulate)), _stream(x, y, stream=stream)))
+    return x
+
+
+def fdk(geom: Geometry, y, views: Sequence[int], x=None, stream=None):
+    """FDK reconstruction from the projections y[len(views)][nv][nu] of the
+    listed views; returns x [nz][ny][nx] float32 (allocated like y if None)."""
+    v = _views(views)
+    if x is None:
+        x = _like(y, geom.vol_shape, F32)
+    if _dtype_code(x) != F32:
+        raise TypeError("fdk output must be float32")
+    _check(lib.fdk(geom.handle, _ptr(y), _dtype_code(y), v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                   v.size, _ptr(x), _stream(x, y, stream=stream)))
     return x
 
 

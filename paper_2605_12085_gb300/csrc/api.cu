@@ -505,6 +505,77 @@ extern "C" fbl_status project(const fbl_geometry *g, const void *x, int32_t x_dt
     return FBL_OK;
 }
 
+extern "C" fbl_status fdk(const fbl_geometry *g, const void *y, int32_t y_dtype, const int32_t *views,
+                          int32_t n_sel, float *x, void *stream) {
+    if (!g || !x || (n_sel > 0 && !y) || (n_sel > 0 && !views)) return fail(FBL_E_INVAL, "fdk: null argument");
+    if (!valid_dtype(y_dtype)) return fail(FBL_E_INVAL, "fdk: bad dtype");
+    fbl_status st = check_views(g, views, n_sel);
+    if (st) return st;
+    if ((st = check_device(g->device))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fbl_geometry_desc &d = g->desc;
+    const size_t nvox = (size_t)d.nx * d.ny * d.nz;
+    const bool x_dev = is_device_ptr(x);
+    AsyncBuf xs, gz, qt, vbuf, ys;
+    float *xd = x;
+    if (!x_dev) {
+        CK(xs.alloc(nvox * sizeof(float), s), "output staging");
+        xd = (float *)xs.p;
+    }
+    if (n_sel == 0) {
+        CK(cudaMemsetAsync(xd, 0, nvox * sizeof(float), s), "memset");
+    } else {
+        // dtheta of each selected view: half the circular gaps to its neighbours
+        std::vector<std::pair<double, int>> ang(n_sel);
+        for (int q = 0; q < n_sel; ++q) {
+            double a = std::fmod(view_angle(d, g->angles, views[q]), 2.0 * M_PI);
+            if (a < 0) a += 2.0 * M_PI;
+            ang[q] = {a, q};
+        }
+        std::sort(ang.begin(), ang.end());
+        std::vector<double> csw(3 * (size_t)n_sel);
+        for (int r = 0; r < n_sel; ++r) {
+            const int q = ang[r].second;
+            double w = 2.0 * M_PI;
+            if (n_sel > 1) {
+                const double nxt = r + 1 < n_sel ? ang[r + 1].first : ang[0].first + 2.0 * M_PI;
+                const double prv = r > 0 ? ang[r - 1].first : ang[n_sel - 1].first - 2.0 * M_PI;
+                w = 0.5 * (nxt - prv);
+            }
+            const double th = view_angle(d, g->angles, views[q]);
+            csw[3 * q + 0] = std::cos(th);
+            csw[3 * q + 1] = std::sin(th);
+            csw[3 * q + 2] = 0.5 * w;
+        }
+        CK(vbuf.alloc(csw.size() * sizeof(double), s), "view table");
+        CK(cudaMemcpyAsync(vbuf.p, csw.data(), csw.size() * sizeof(double), cudaMemcpyHostToDevice, s),
+           "view table");
+        const size_t per_view_in = (size_t)d.nv * d.nu * dtype_size(y_dtype);
+        const void *yd = nullptr;
+        if ((st = device_input(y, per_view_in * n_sel, ys, &yd, s))) return st;
+        const int chunk = std::min<int>(n_sel, 256);  // bounds the filtered-projection scratch
+        CK(qt.alloc(fdk_filtered_elems(chunk, d.nu, d.nv) * sizeof(float), s), "filtered projections");
+        CK(gz.alloc(nvox * sizeof(float), s), "volume scratch");
+        for (int v0 = 0; v0 < n_sel; v0 += chunk) {
+            const int nc = std::min(chunk, n_sel - v0);
+            CK(cudaMemsetAsync(qt.p, 0, fdk_filtered_elems(nc, d.nu, d.nv) * sizeof(float), s), "memset");
+            CK(launch_fdk_filter((const char *)yd + per_view_in * v0, y_dtype, nc, d.nu, d.nv, d.sod, d.sdd, d.du,
+                                 d.dv, (float *)qt.p, s),
+               "fdk filter kernel");
+            CK(launch_fdk_bp((const float *)qt.p, (const double *)vbuf.p + 3 * (size_t)v0, nc, d.nx, d.ny, d.nz,
+                             d.nu, d.nv, d.vx, d.vy, d.vz, d.sod, d.sdd, d.du, d.dv, v0 > 0 ? 1 : 0,
+                             (float *)gz.p, s),
+               "fdk backprojection kernel");
+        }
+        CK(launch_zi_to_natural((const float *)gz.p, xd, d.nx, d.ny, d.nz, 0, s), "reorder");
+    }
+    if (!x_dev) {
+        CK(cudaMemcpyAsync(x, xd, nvox * sizeof(float), cudaMemcpyDeviceToHost, s), "x D2H");
+        CK(cudaStreamSynchronize(s), "fdk");
+    }
+    return FBL_OK;
+}
+
 extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_dtype,
                                   const int32_t *views, int32_t n_sel, float *x,
                                   int32_t accumulate, void *stream) {

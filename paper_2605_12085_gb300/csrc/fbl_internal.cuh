@@ -336,6 +336,17 @@ cudaError_t launch_batch_ls_init(BatchHdr *hdr, BatchVol *vols, int n_vol, cudaS
 cudaError_t launch_batch_decide(BatchHdr *hdr, BatchVol *vols, int n_vol,
                                 cudaGraphConditionalHandle cond, cudaStream_t st);
 
+// FDK (k_fdk.cu): weighted, ramp-filtered projections of n_sel views written
+// transposed with a zero border, qt[s][iu + 1][iv + 1] (rows of nv + 2);
+// then the weighted backprojection of them into gzi[j][i][k] (= or +=).
+// view_csw: n_sel x (cos, sin, dtheta / 2) in FP64.
+size_t fdk_filtered_elems(int n_sel, int nu, int nv);
+cudaError_t launch_fdk_filter(const void *y, int y_dtype, int n_sel, int nu, int nv, double sod, double sdd,
+                              double du, double dv, float *qt, cudaStream_t st);
+cudaError_t launch_fdk_bp(const float *qt, const double *view_csw, int n_sel, int nx, int ny, int nz, int nu,
+                          int nv, double vx, double vy, double vz, double sod, double sdd, double du, double dv,
+                          int accumulate, float *gzi, cudaStream_t st);
+
 // Record the message returned by fbl_last_error() on this thread.
 void set_last_error(const char *msg);
 

@@ -75,3 +75,22 @@ def test_uniform_ball_from_exact_projections():
     # the sampled-voxel form gives the same values
     vox = [(g.nz // 2, 24, 24), (g.nz // 2, 10, 30), (0, 5, 5)]
     assert np.allclose(fdk.fdk(g, y, range(g.n_views), voxels=vox), [f[v] for v in vox], rtol=0, atol=1e-12)
+
+
+def test_filter_equals_direct_convolution():
+    # the FFT form of step 2 against the convolution sum written out
+    g = synth.Geometry(nx=8, ny=8, nz=8, vx=1.0, vy=1.0, vz=1.0, n_views=2, sod=300.0, sdd=450.0,
+                       nu=37, nv=5, du=1.2, dv=1.1)
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal((2, g.nv, g.nu))
+    q = fdk.filtered(g, y, [0, 1])
+    m = g.sod / g.sdd
+    t = g.du * m
+    h = fdk.ramp_kernel(g.nu, t)
+    a = (np.arange(g.nu) - (g.nu - 1) / 2) * g.du * m
+    b = (np.arange(g.nv) - (g.nv - 1) / 2) * g.dv * m
+    for s in range(2):
+        for r in range(g.nv):
+            pw = y[s, r] * g.sod / np.sqrt(g.sod ** 2 + a ** 2 + b[r] ** 2)
+            direct = [t * sum(h[(i - n) + g.nu - 1] * pw[n] for n in range(g.nu)) for i in range(g.nu)]
+            assert np.allclose(q[s, r], direct, rtol=1e-12, atol=1e-12 * np.abs(direct).max())
