@@ -419,6 +419,31 @@ def batched_records(fbl, device):
             "c5s_plain": batched_record(fbl, device, synth.batched_small_workloads(), small)}
 
 
+def fdk_record(fbl, G, g, b, xt, device, reps=2):
+    """FDK over all views of the workload (the paper's analytic baseline):
+    time per reconstruction (CUDA events, one warm-up), voxel-views per second,
+    and its relative error against the phantom."""
+    import torch
+    stream = torch.cuda.current_stream(device)
+    views = list(range(g.n_views))
+    x = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
+    fbl.fdk(G, b, views, x=x)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fbl.fdk(G, b, views, x=x)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / reps
+    xt_d = torch.from_numpy(xt).to(device)
+    re = float(torch.linalg.vector_norm(x - xt_d) / torch.linalg.vector_norm(xt_d))
+    del x, xt_d
+    return {"views": g.n_views, "ms": ms, "gups_voxel_views": float(g.n_views) * g.n_vox / (ms * 1e-3) / 1e9,
+            "rel_error_vs_phantom": re}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -738,6 +763,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         out["full_sweep"] = full_sweep(fbl, G, g, x, device)
+        out["fdk"] = fdk_record(fbl, G, g, b, xt, device)
 
     # storage-precision variants (BF16 / FP16 iterates and data, FP32 arithmetic)
     if args.variants:

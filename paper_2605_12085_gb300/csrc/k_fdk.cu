@@ -11,13 +11,19 @@
 // k_fdk_filter: a block takes FDK_ROWS consecutive detector rows of one view,
 // stages the weighted rows in shared memory and every thread forms the
 // filtered values of its columns for all of them (the odd-tap coefficients
-// are shared by the rows).  It writes q transposed, zero-bordered:
-// qt[s][iu + 1][iv + 1] with rows of nv + 2, so the backprojection reads
-// consecutive detector rows along z and needs no bounds test at the edges.
-// k_fdk_bp (= or += over chunks of views): a warp owns one (i, j) voxel column and 32 * FDK_KPL voxels along
-// z (lane l: k0 + l + 32 t); the per-view geometry of the column (detector
-// column, its weight, the vertical map k -> v) is computed once per warp in
-// FP64, each lane interpolates bilinearly.  Output in [j][i][k] order.
+// are shared by the rows).  It writes q transposed, as column pairs:
+// entry (s, c, e) = (q(c - 1, e - 2), q(c, e - 2)) for c = 0 .. nu and rows of
+// fdk_row_stride(nv) entries, zero outside the detector, so the
+// backprojection reads the four taps of a voxel as two aligned float2 loads of
+// consecutive entries along z and needs no bounds test at the edges.  The
+// block restages its results in shared memory and stores them as float4s.
+// k_fdk_bp (= or += over chunks of views): a warp owns one (i, j) voxel
+// column and 32 * FDK_KPL voxels along z (lane l: k0 + l + 32 t).  The FP64
+// geometry of a (column, view) pair (detector column and weight, the
+// vertical map k -> v) is formed by one thread -- lane l of the warp takes
+// view s0 + l -- and kept in shared memory for the warp, so FP64 work (slow
+// on this part) costs one thread per pair instead of a whole warp; every lane
+// then interpolates bilinearly in FP32.  Output in [j][i][k] order.
 #include <math.h>
 
 #include "fbl_internal.cuh"
@@ -29,6 +35,12 @@ constexpr int FDK_ROWS = 8;    // detector rows per filter block
 constexpr int FDK_FT = 256;    // filter block threads
 constexpr int FDK_KPL = 8;     // voxels per lane along z in the backprojection
 constexpr int FDK_WARPS = 8;   // voxel columns (consecutive i) per backprojection block
+constexpr int FDK_VB = 32;     // views whose pair geometry a block forms at once (one per lane)
+
+// float2 entries per detector column of the filtered projections: row v at
+// entry v + 2, two zero entries below row 0 and at least two above row nv - 1,
+// even so that every column starts on a 16-byte boundary
+__host__ __device__ inline int fdk_row_stride(int nv) { return (nv + 5) & ~1; }
 
 template <typename TY>
 __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y, int nu, int nv,
@@ -36,7 +48,8 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
                                                        double cv, float *__restrict__ qt) {
     extern __shared__ float fsm[];
     float *P = fsm;                       // [FDK_ROWS][nu] weighted rows
-    float *C = fsm + FDK_ROWS * nu;       // [nu/2 + 1] t * h((2j+1) t)
+    float *Q = fsm + FDK_ROWS * nu;       // [FDK_ROWS][nu] filtered rows
+    float *C = fsm + 2 * FDK_ROWS * nu;   // [nu/2 + 1] t * h((2j+1) t)
     const int s = blockIdx.y, r0 = blockIdx.x * FDK_ROWS;
     const double t = du_m;
     const int nodd = nu / 2 + 1;
@@ -48,9 +61,11 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
         const int r = e / nu, iu = e - r * nu, iv = r0 + r;
         float val = 0.f;
         if (iv < nv) {
+            // cosine weight in FP32 (relative error ~3e-7): FP64 square roots
+            // and divisions are slow on this part
             const double a = (iu - cu) * du_m, b = (iv - cv) * dv_m;
-            const double w = sod / sqrt(sod * sod + a * a + b * b);
-            val = (float)w * to_f32(y[((size_t)s * nv + iv) * nu + iu]);
+            const float w = (float)sod * rsqrtf((float)(sod * sod + a * a + b * b));
+            val = w * to_f32(y[((size_t)s * nv + iv) * nu + iu]);
         }
         P[r * nu + iu] = val;
     }
@@ -71,10 +86,23 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
                 acc[r] = fmaf(c, pl + pr, acc[r]);
             }
         }
-        float *out = qt + ((size_t)s * (nu + 2) + iu + 1) * (nv + 2) + 1 + r0;
 #pragma unroll
-        for (int r = 0; r < FDK_ROWS; ++r)
-            if (r0 + r < nv) out[r] = acc[r];
+        for (int r = 0; r < FDK_ROWS; ++r) Q[r * nu + iu] = acc[r];
+    }
+    __syncthreads();
+    // column pairs (c - 1, c) of row pairs (r0 + 2p, r0 + 2p + 1) as one float4;
+    // rows at or past nv keep the zeros of the cleared buffer
+    const int rs = fdk_row_stride(nv);
+    float2 *out2 = reinterpret_cast<float2 *>(qt) + (size_t)s * (nu + 1) * rs + r0 + 2;
+    for (int e = threadIdx.x; e < (nu + 1) * (FDK_ROWS / 2); e += FDK_FT) {
+        const int c = e / (FDK_ROWS / 2), p = e - c * (FDK_ROWS / 2), r = 2 * p;
+        if (r0 + r >= nv) continue;
+        float4 v;
+        v.x = c > 0 ? Q[r * nu + c - 1] : 0.f;
+        v.y = c < nu ? Q[r * nu + c] : 0.f;
+        v.z = c > 0 ? Q[(r + 1) * nu + c - 1] : 0.f;
+        v.w = c < nu ? Q[(r + 1) * nu + c] : 0.f;
+        *reinterpret_cast<float4 *>(out2 + (size_t)c * rs + r) = v;
     }
 }
 
@@ -82,54 +110,87 @@ struct FdkView {
     double c, s, w;  // cos, sin, dtheta / 2
 };
 
-__global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float *__restrict__ qt, const FdkView *views,
+struct FdkPair {
+    int off;          // entry of (column iu0 + 1, row 0) in the view's block; -1: off the detector
+    float tu, w, dfv; // horizontal weight, (dtheta/2) / U^2, rows per voxel along z
+};
+struct FdkBase {
+    int ib;    // floor of the detector row of voxel k0 + 32 q
+    float fb;  // and its fraction
+};
+
+__global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float2 *__restrict__ qt, const FdkView *views,
                                                            int n_sel, int nx, int ny, int nz, int nu, int nv,
                                                            double vx, double vy, double vz, double sod,
-                                                           double du_m, double dv_m, double cu, double cv,
+                                                           double inv_du_m, double inv_dv_m, double cu, double cv,
                                                            int accumulate, float *__restrict__ gzi) {
-    const int lane = threadIdx.x, i = blockIdx.x * FDK_WARPS + threadIdx.y, j = blockIdx.y;
+    __shared__ FdkPair hp[FDK_WARPS][FDK_VB];
+    __shared__ FdkBase hb[FDK_WARPS][FDK_KPL][FDK_VB];
+    const int lane = threadIdx.x, wi = threadIdx.y;
+    const int i = blockIdx.x * FDK_WARPS + wi, j = blockIdx.y;
     const int k0 = blockIdx.z * 32 * FDK_KPL;
-    if (i >= nx) return;  // whole warp
+    const bool col = i < nx;  // columns past nx still take part in the barriers
     const double x = (i - 0.5 * (nx - 1)) * vx, yy = (j - 0.5 * (ny - 1)) * vy;
     const double czk = 0.5 * (nz - 1);
+    const int rs = fdk_row_stride(nv);
+    const size_t vstride = (size_t)(nu + 1) * rs;
     float acc[FDK_KPL];
 #pragma unroll
     for (int q = 0; q < FDK_KPL; ++q) acc[q] = 0.f;
-    const size_t vstride = (size_t)(nu + 2) * (nv + 2);
-    for (int s = 0; s < n_sel; ++s) {
-        const FdkView v = views[s];
-        const double xi = x * v.c + yy * v.s, eta = -x * v.s + yy * v.c;
-        const double invU = sod / (sod - xi);
-        const double fu = eta * invU / du_m + cu;
-        if (!(fu > -1.0 && fu < (double)nu)) continue;  // the column projects off the detector
-        const double fl = floor(fu);
-        const int iu0 = (int)fl;
-        const float tu = (float)(fu - fl);
-        const float w = (float)(v.w * invU * invU);
-        // detector row of voxel k: fv = fv0 + k * dfv, as an exact FP64 base per
-        // 32 voxels (warp-uniform) plus a small FP32 offset per lane
-        const double dfv = vz * invU / dv_m;
-        const double fv0 = cv - czk * dfv;
-        const float dfv_f = (float)dfv;
-        const float *c0 = qt + (size_t)s * vstride + (size_t)(iu0 + 1) * (nv + 2) + 1;
-        const float *c1 = c0 + (nv + 2);
+    for (int s0 = 0; s0 < n_sel; s0 += FDK_VB) {
+        const int nb = min(FDK_VB, n_sel - s0);
+        if (lane < nb) {
+            const FdkView v = views[s0 + lane];
+            const double xi = x * v.c + yy * v.s, eta = -x * v.s + yy * v.c;
+            const double invU = sod / (sod - xi);
+            const double fu = eta * invU * inv_du_m + cu;
+            FdkPair p;
+            p.off = -1;
+            p.tu = p.w = p.dfv = 0.f;
+            if (fu > -1.0 && fu < (double)nu) {
+                const double fl = floor(fu);
+                p.off = ((int)fl + 1) * rs + 2;
+                p.tu = (float)(fu - fl);
+                p.w = (float)(v.w * invU * invU);
+                // detector row of voxel k: fv0 + k * dfv, as an exact FP64 base
+                // per 32 voxels plus a small FP32 offset per lane
+                const double dfv = vz * invU * inv_dv_m;
+                const double fv0 = cv - czk * dfv;
+                p.dfv = (float)dfv;
 #pragma unroll
-        for (int q = 0; q < FDK_KPL; ++q) {
-            const int k = k0 + lane + 32 * q;
-            const double bq = fv0 + (double)(k0 + 32 * q) * dfv;
-            const double bi = floor(bq);
-            const float fl = (float)(bq - bi) + (float)lane * dfv_f;  // |.| <= 1 + 31 dfv
-            const float fll = floorf(fl);
-            const int iv0 = (int)bi + (int)fll;
-            if (k < nz && iv0 >= -1 && iv0 <= nv - 1) {
-                const float tv = fl - fll;
-                const float a0 = __ldg(c0 + iv0), a1 = __ldg(c0 + iv0 + 1);
-                const float b0 = __ldg(c1 + iv0), b1 = __ldg(c1 + iv0 + 1);
-                const float lo = fmaf(tv, a1 - a0, a0), hi = fmaf(tv, b1 - b0, b0);
-                acc[q] = fmaf(w, fmaf(tu, hi - lo, lo), acc[q]);
+                for (int q = 0; q < FDK_KPL; ++q) {
+                    const double bq = fv0 + (double)(k0 + 32 * q) * dfv;
+                    const double bi = floor(bq);
+                    hb[wi][q][lane] = FdkBase{(int)bi, (float)(bq - bi)};
+                }
+            }
+            hp[wi][lane] = p;
+        }
+        __syncthreads();
+        if (col) {
+            for (int t = 0; t < nb; ++t) {
+                const FdkPair p = hp[wi][t];
+                if (p.off < 0) continue;
+                const float2 *col2 = qt + (size_t)(s0 + t) * vstride + p.off;
+                const float lf = (float)lane * p.dfv;  // |.| <= 31 dfv
+#pragma unroll
+                for (int q = 0; q < FDK_KPL; ++q) {
+                    const FdkBase bb = hb[wi][q][t];
+                    const float fl = bb.fb + lf;
+                    const float fll = floorf(fl);
+                    const int iv0 = bb.ib + (int)fll;
+                    if (k0 + lane + 32 * q < nz && iv0 >= -1 && iv0 <= nv - 1) {
+                        const float tv = fl - fll;
+                        const float2 A = __ldg(col2 + iv0), B = __ldg(col2 + iv0 + 1);  // rows iv0, iv0 + 1
+                        const float lo = fmaf(tv, B.x - A.x, A.x), hi = fmaf(tv, B.y - A.y, A.y);
+                        acc[q] = fmaf(p.w, fmaf(p.tu, hi - lo, lo), acc[q]);
+                    }
+                }
             }
         }
+        __syncthreads();
     }
+    if (!col) return;
     float *out = gzi + ((size_t)j * nx + i) * nz;
 #pragma unroll
     for (int q = 0; q < FDK_KPL; ++q) {
@@ -140,13 +201,13 @@ __global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float *__restri
 
 }  // namespace
 
-size_t fdk_filtered_elems(int n_sel, int nu, int nv) { return (size_t)n_sel * (nu + 2) * (nv + 2); }
+size_t fdk_filtered_elems(int n_sel, int nu, int nv) { return (size_t)n_sel * (nu + 1) * fdk_row_stride(nv) * 2; }
 
 cudaError_t launch_fdk_filter(const void *y, int y_dtype, int n_sel, int nu, int nv, double sod, double sdd,
                               double du, double dv, float *qt, cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
     const double m = sod / sdd;
-    const size_t smem = ((size_t)FDK_ROWS * nu + nu / 2 + 1) * sizeof(float);
+    const size_t smem = ((size_t)2 * FDK_ROWS * nu + nu / 2 + 1) * sizeof(float);
     dim3 grid((nv + FDK_ROWS - 1) / FDK_ROWS, n_sel);
     const double cu = 0.5 * (nu - 1), cv = 0.5 * (nv - 1);
     cudaError_t e = cudaSuccess;
@@ -181,8 +242,9 @@ cudaError_t launch_fdk_bp(const float *qt, const double *view_csw, int n_sel, in
     const double m = sod / sdd;
     dim3 block(32, FDK_WARPS);
     dim3 grid((nx + FDK_WARPS - 1) / FDK_WARPS, ny, (nz + 32 * FDK_KPL - 1) / (32 * FDK_KPL));
-    k_fdk_bp<<<grid, block, 0, st>>>(qt, (const FdkView *)view_csw, n_sel, nx, ny, nz, nu, nv, vx, vy, vz, sod,
-                                     du * m, dv * m, 0.5 * (nu - 1), 0.5 * (nv - 1), accumulate, gzi);
+    k_fdk_bp<<<grid, block, 0, st>>>((const float2 *)qt, (const FdkView *)view_csw, n_sel, nx, ny, nz, nu, nv, vx,
+                                     vy, vz, sod, 1.0 / (du * m), 1.0 / (dv * m), 0.5 * (nu - 1), 0.5 * (nv - 1),
+                                     accumulate, gzi);
     return cudaGetLastError();
 }
 
