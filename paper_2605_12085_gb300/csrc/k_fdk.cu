@@ -111,7 +111,7 @@ struct FdkView {
 };
 
 struct FdkPair {
-    int off;          // entry of (column iu0 + 1, row 0) in the view's block; -1: off the detector
+    int off;          // entry of (column iu0 + 1, row 0) in the view's block
     float tu, w, dfv; // horizontal weight, (dtheta/2) / U^2, rows per voxel along z
 };
 struct FdkBase {
@@ -144,33 +144,34 @@ __global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float2 *__restr
             const double xi = x * v.c + yy * v.s, eta = -x * v.s + yy * v.c;
             const double invU = sod / (sod - xi);
             const double fu = eta * invU * inv_du_m + cu;
-            FdkPair p;
-            p.off = -1;
-            p.tu = p.w = p.dfv = 0.f;
-            if (fu > -1.0 && fu < (double)nu) {
+            // a column that projects off the detector reads column 0 with
+            // weight 0 and rows that fail the range test below
+            FdkPair p{2, 0.f, 0.f, 0.f};
+            const bool on = fu > -1.0 && fu < (double)nu;
+            const double dfv = vz * invU * inv_dv_m;
+            if (on) {
                 const double fl = floor(fu);
                 p.off = ((int)fl + 1) * rs + 2;
                 p.tu = (float)(fu - fl);
                 p.w = (float)(v.w * invU * invU);
-                // detector row of voxel k: fv0 + k * dfv, as an exact FP64 base
-                // per 32 voxels plus a small FP32 offset per lane
-                const double dfv = vz * invU * inv_dv_m;
-                const double fv0 = cv - czk * dfv;
                 p.dfv = (float)dfv;
+            }
+            // detector row of voxel k: fv0 + k * dfv, as an exact FP64 base per
+            // 32 voxels plus a small FP32 offset per lane
+            const double fv0 = cv - czk * dfv;
 #pragma unroll
-                for (int q = 0; q < FDK_KPL; ++q) {
-                    const double bq = fv0 + (double)(k0 + 32 * q) * dfv;
-                    const double bi = floor(bq);
-                    hb[wi][q][lane] = FdkBase{(int)bi, (float)(bq - bi)};
-                }
+            for (int q = 0; q < FDK_KPL; ++q) {
+                const double bq = fv0 + (double)(k0 + 32 * q) * dfv;
+                const double bi = floor(bq);
+                hb[wi][q][lane] = on ? FdkBase{(int)bi, (float)(bq - bi)} : FdkBase{-(1 << 30), 0.f};
             }
             hp[wi][lane] = p;
         }
         __syncthreads();
         if (col) {
+#pragma unroll 2
             for (int t = 0; t < nb; ++t) {
                 const FdkPair p = hp[wi][t];
-                if (p.off < 0) continue;
                 const float2 *col2 = qt + (size_t)(s0 + t) * vstride + p.off;
                 const float lf = (float)lane * p.dfv;  // |.| <= 31 dfv
 #pragma unroll
@@ -179,12 +180,16 @@ __global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float2 *__restr
                     const float fl = bb.fb + lf;
                     const float fll = floorf(fl);
                     const int iv0 = bb.ib + (int)fll;
-                    if (k0 + lane + 32 * q < nz && iv0 >= -1 && iv0 <= nv - 1) {
-                        const float tv = fl - fll;
-                        const float2 A = __ldg(col2 + iv0), B = __ldg(col2 + iv0 + 1);  // rows iv0, iv0 + 1
-                        const float lo = fmaf(tv, B.x - A.x, A.x), hi = fmaf(tv, B.y - A.y, A.y);
-                        acc[q] = fmaf(p.w, fmaf(p.tu, hi - lo, lo), acc[q]);
-                    }
+                    // taps clamped into the column so the loads need no branch;
+                    // a voxel whose rows fall off the detector keeps its sum
+                    // (lanes past nz accumulate values that are never stored)
+                    const bool ok = iv0 >= -1 && iv0 <= nv - 1;
+                    const int ivc = min(max(iv0, -1), nv - 1);
+                    const float tv = fl - fll;
+                    const float2 A = __ldg(col2 + ivc), B = __ldg(col2 + ivc + 1);  // rows iv0, iv0 + 1
+                    const float lo = fmaf(tv, B.x - A.x, A.x), hi = fmaf(tv, B.y - A.y, A.y);
+                    const float nxt = fmaf(p.w, fmaf(p.tu, hi - lo, lo), acc[q]);
+                    acc[q] = ok ? nxt : acc[q];
                 }
             }
         }
