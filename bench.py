@@ -328,7 +328,8 @@ def paper_cases_record(fbl, device, budget_s=30.0):
     FB on the full batch (step 0.9/L).  Reported: RE = ||x - x_true|| /
     ||x_true|| and PSNR = 10 log10(max(x_true)^2 / MSE) at fixed times and at
     iterations 120 and 240 (the paper's 120 s / 240 s budgets ran at about one
-    iteration per second), and the best RE seen."""
+    iteration per second), and the best RE seen.  Also FDK on the case's
+    views (time, RE, PSNR) and plain FB-LISA started from that FDK volume."""
     import math
     import torch
     import synth
@@ -359,11 +360,26 @@ def paper_cases_record(fbl, device, budget_s=30.0):
             mse = re * re * xt_n2 / g.n_vox
             return 10.0 * math.log10(peak2 / mse) if mse > 0 else float("inf")
 
-        def run(params, fast=False):
+        # FDK on the case's (undersampled) views: the paper's analytic baseline,
+        # and a warm start for FB-LISA
+        x_fdk = fbl.fdk(G, b, views)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fbl.fdk(G, b, views, x=x_fdk)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        re_fdk = float(torch.linalg.vector_norm(x_fdk - xt_d) / torch.linalg.vector_norm(xt_d))
+        fdk_rec = {"ms": e0.elapsed_time(e1), "rel_error": re_fdk, "psnr_db": None}
+
+        def run(params, fast=False, x0=None):
             S = fbl.fblisa_create(G, params)
             if fast:
                 S.set_proposal(net, margin=0.25)
             x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32, device=device)
+            if x0 is not None:
+                x.copy_(x0)
             bb = b16 if fast else b
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -402,8 +418,10 @@ def paper_cases_record(fbl, device, budget_s=30.0):
             "fblisa_fast": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, x_dtype=fbl.BF16, b_dtype=fbl.BF16,
                                                   use_graph=1, proposal=1, **base), fast=True),
             "fb_fixed_full_batch": run(fbl.params_default(alpha0=0.9 / L, N0=g.n_views, fixed_step=1, **base)),
+            "fdk": dict(fdk_rec, psnr_db=psnr(re_fdk)),
+            "fblisa_fp32_from_fdk": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, **base), x0=x_fdk),
         }
-        del G, b, b16, xt_d
+        del G, b, b16, xt_d, x_fdk
         torch.cuda.empty_cache()
     return out
 
