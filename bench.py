@@ -70,6 +70,8 @@ def parse():
                     help="also run the paper-shaped 560^3 cases with RE / PSNR over time (several minutes)")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
+    ap.add_argument("--fdk-only", type=int, default=0,
+                    help="time only FDK over all views of --workload (--steps reconstructions after one warm-up)")
     return ap.parse_args()
 
 
@@ -688,6 +690,20 @@ def aggregate_ranks(ms, units, dist=None):
     return float(t[0]), float(u[0])
 
 
+def run_fdk_only(args):
+    """FDK alone on the workload's data (one GPU): a side measurement, not the
+    contract line."""
+    import torch
+    import paper_2605_12085_gb300 as fbl
+    import synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS[args.workload]
+    G, xt, b = make_data(fbl, wl, device)
+    rec = fdk_record(fbl, G, wl.geom, b, xt, device, reps=max(1, args.steps))
+    return {"workload": args.workload, "fdk": rec}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -924,6 +940,10 @@ def main():
         if rank != 0:
             return 0
         print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if args.fdk_only:
+        if rank == 0:
+            print(json.dumps(run_fdk_only(args)), flush=True)
         return 0
     if world > 1:
         import torch.distributed as dist

@@ -156,14 +156,18 @@ __global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float2 *__restr
                 p.w = (float)(v.w * invU * invU);
                 p.dfv = (float)dfv;
             }
-            // detector row of voxel k: fv0 + k * dfv, as an exact FP64 base per
-            // 32 voxels plus a small FP32 offset per lane
+            // detector row of voxel k: fv0 + k * dfv, as a base per 32 voxels in
+            // Q32 fixed point (error <= 2^-33 (1 + 32 q) rows from rounding the
+            // start and the step) plus a small FP32 offset per lane: integer
+            // steps instead of FP64 ones per base
             const double fv0 = cv - czk * dfv;
+            const long long D = __double2ll_rn(dfv * 4294967296.0);
+            long long B = __double2ll_rn((fv0 + (double)k0 * dfv) * 4294967296.0);
 #pragma unroll
-            for (int q = 0; q < FDK_KPL; ++q) {
-                const double bq = fv0 + (double)(k0 + 32 * q) * dfv;
-                const double bi = floor(bq);
-                hb[wi][q][lane] = on ? FdkBase{(int)bi, (float)(bq - bi)} : FdkBase{-(1 << 30), 0.f};
+            for (int q = 0; q < FDK_KPL; ++q, B += 32 * D) {
+                const int ib = (int)(B >> 32);
+                const float fb = (float)(unsigned)(B & 0xffffffffLL) * 2.3283064365386963e-10f;  // 2^-32
+                hb[wi][q][lane] = on ? FdkBase{ib, fb} : FdkBase{-(1 << 30), 0.f};
             }
             hp[wi][lane] = p;
         }
