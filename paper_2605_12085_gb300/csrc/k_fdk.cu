@@ -119,7 +119,7 @@ struct FdkBase {
     float fb;  // and its fraction
 };
 
-__global__ void __launch_bounds__(32 * FDK_WARPS) k_fdk_bp(const float2 *__restrict__ qt, const FdkView *views,
+__global__ void __launch_bounds__(32 * FDK_WARPS, 5) k_fdk_bp(const float2 *__restrict__ qt, const FdkView *views,
                                                            int n_sel, int nx, int ny, int nz, int nu, int nv,
                                                            double vx, double vy, double vz, double sod,
                                                            double inv_du_m, double inv_dv_m, double cu, double cv,
