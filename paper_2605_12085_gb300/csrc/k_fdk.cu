@@ -8,10 +8,11 @@
 //   f(x) = sum_views (dtheta/2) q(eta/U, z/U) / U^2,
 //       U = (SOD - xi)/SOD, xi = x cos + y sin, eta = -x sin + y cos.
 //
-// k_fdk_filter: a block takes FDK_ROWS consecutive detector rows of one view,
-// stages the weighted rows in shared memory and every thread forms the
-// filtered values of its columns for all of them (the odd-tap coefficients
-// are shared by the rows).  It writes q transposed, as column pairs:
+// k_fdk_filter: a block takes FDK_ROWS consecutive detector rows of one view
+// and stages the weighted rows in shared memory; each thread forms 8 filtered
+// values of one row (same parity, two columns apart) from a sliding window of
+// coefficients in registers, so one shared-memory read feeds 8 FMAs.  It
+// writes q transposed, as column pairs:
 // entry (s, c, e) = (q(c - 1, e - 2), q(c, e - 2)) for c = 0 .. nu and rows of
 // fdk_row_stride(nv) entries, zero outside the detector, so the
 // backprojection reads the four taps of a voxel as two aligned float2 loads of
@@ -42,52 +43,77 @@ constexpr int FDK_VB = 32;     // views whose pair geometry a block forms at onc
 // even so that every column starts on a 16-byte boundary
 __host__ __device__ inline int fdk_row_stride(int nv) { return (nv + 5) & ~1; }
 
+// The filter's row staging: FR_PAD zero columns on each side of a row, and
+// one unused word after every 16 columns so that lanes 16 columns apart fall
+// in different shared-memory banks.
+constexpr int FR_PAD = 256;
+constexpr int FR_E = 8;  // outputs per thread: columns i0, i0 + 2, .., i0 + 14
+__device__ __forceinline__ int fr_addr(int c) { return c + (c >> 4); }
+__host__ __device__ inline int fr_row_len(int nu) { return (nu + 2 * FR_PAD - 1) + ((nu + 2 * FR_PAD - 1) >> 4) + 1; }
+__host__ __device__ inline int fr_kh(int nu) { return (nu + FR_PAD + 2 * FR_E - 1) | 1; }  // odd
+
 template <typename TY>
 __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y, int nu, int nv,
                                                        double sod, double du_m, double dv_m, double cu,
                                                        double cv, float *__restrict__ qt) {
     extern __shared__ float fsm[];
-    float *P = fsm;                       // [FDK_ROWS][nu] weighted rows
-    float *Q = fsm + FDK_ROWS * nu;       // [FDK_ROWS][nu] filtered rows
-    float *C = fsm + 2 * FDK_ROWS * nu;   // [nu/2 + 1] t * h((2j+1) t)
+    const int lp = nu + 2 * FR_PAD, rl = fr_row_len(nu), KH = fr_kh(nu);
+    float *P = fsm;                      // [FDK_ROWS][rl] weighted rows, padded and skewed
+    float *Q = fsm + FDK_ROWS * rl;      // [FDK_ROWS][nu] filtered rows
+    float *H = Q + FDK_ROWS * nu;        // t h(k t) for odd k in [-KH, KH], at (k + KH) / 2
     const int s = blockIdx.y, r0 = blockIdx.x * FDK_ROWS;
     const double t = du_m;
-    const int nodd = nu / 2 + 1;
-    for (int j = threadIdx.x; j < nodd; j += FDK_FT) {
-        const double k = 2.0 * j + 1.0;
-        C[j] = (float)(-1.0 / (M_PI * M_PI * k * k * t));
+    for (int j = threadIdx.x; j <= KH; j += FDK_FT) {
+        const double k = 2.0 * j - KH;
+        H[j] = (float)(-1.0 / (M_PI * M_PI * k * k * t));
     }
-    for (int e = threadIdx.x; e < FDK_ROWS * nu; e += FDK_FT) {
-        const int r = e / nu, iu = e - r * nu, iv = r0 + r;
+    // cosine weight in FP32 (relative error below 1e-6): FP64 arithmetic is
+    // slow on this part
+    const float sodf = (float)sod, sod2 = (float)(sod * sod), duf = (float)du_m, dvf = (float)dv_m;
+    const float cuf = (float)cu, cvf = (float)cv;
+    for (int e = threadIdx.x; e < FDK_ROWS * lp; e += FDK_FT) {
+        const int r = e / lp, c = e - r * lp, iu = c - FR_PAD, iv = r0 + r;
         float val = 0.f;
-        if (iv < nv) {
-            // cosine weight in FP32 (relative error ~3e-7): FP64 square roots
-            // and divisions are slow on this part
-            const double a = (iu - cu) * du_m, b = (iv - cv) * dv_m;
-            const float w = (float)sod * rsqrtf((float)(sod * sod + a * a + b * b));
+        if (iv < nv && iu >= 0 && iu < nu) {
+            const float a = ((float)iu - cuf) * duf, b = ((float)iv - cvf) * dvf;
+            const float w = sodf * rsqrtf(fmaf(a, a, fmaf(b, b, sod2)));
             val = w * to_f32(y[((size_t)s * nv + iv) * nu + iu]);
         }
-        P[r * nu + iu] = val;
+        P[r * rl + fr_addr(c)] = val;
     }
     __syncthreads();
+    // A warp takes one row and 256 columns: lane l the 8 outputs i0 + 2e,
+    // i0 = Iw + 16 (l / 2) + l % 2.  Output i sums t h(n - i) P(n) over the odd
+    // offsets n - i (the even ones other than 0 vanish); with d = n - i0 the
+    // coefficient of output e is t h(d - 2e), so as d steps by 2 the 8
+    // coefficients shift by one place and one new one is read (the same for
+    // the whole warp).  d runs over [-Iw - 255, nu - 1 - Iw], which covers
+    // n = 0 .. nu - 1 for every lane; the zero padding supplies the rest.
     const float c0 = (float)(1.0 / (4.0 * t));
-    for (int iu = threadIdx.x; iu < nu; iu += FDK_FT) {
-        float acc[FDK_ROWS];
+    const int nseg = (nu + 255) / 256;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int task = warp; task < FDK_ROWS * nseg; task += FDK_FT / 32) {
+        const int r = task / nseg, Iw = (task - r * nseg) * 256;
+        const int i0 = Iw + 16 * (lane >> 1) + (lane & 1);
+        const float *Pr = P + r * rl;
+        float acc[FR_E], hw[FR_E];
+        const int dmin = -Iw - 255, dmax = nu - 1 - Iw;
 #pragma unroll
-        for (int r = 0; r < FDK_ROWS; ++r) acc[r] = c0 * P[r * nu + iu];
-        for (int j = 0; 2 * j + 1 < nu; ++j) {
-            const int k = 2 * j + 1;
-            const int lft = iu - k, rgt = iu + k;
-            const float c = C[j];
+        for (int e = 0; e < FR_E; ++e) {
+            acc[e] = c0 * Pr[fr_addr(i0 + 2 * e + FR_PAD)];
+            hw[e] = H[(dmin - 2 * e + KH) >> 1];
+        }
+        for (int d = dmin; d <= dmax; d += 2) {
+            const float p = Pr[fr_addr(i0 + d + FR_PAD)];
 #pragma unroll
-            for (int r = 0; r < FDK_ROWS; ++r) {
-                const float pl = lft >= 0 ? P[r * nu + lft] : 0.f;
-                const float pr = rgt < nu ? P[r * nu + rgt] : 0.f;
-                acc[r] = fmaf(c, pl + pr, acc[r]);
-            }
+            for (int e = 0; e < FR_E; ++e) acc[e] = fmaf(hw[e], p, acc[e]);
+#pragma unroll
+            for (int e = FR_E - 1; e > 0; --e) hw[e] = hw[e - 1];
+            hw[0] = H[(d + 2 + KH) >> 1];
         }
 #pragma unroll
-        for (int r = 0; r < FDK_ROWS; ++r) Q[r * nu + iu] = acc[r];
+        for (int e = 0; e < FR_E; ++e)
+            if (i0 + 2 * e < nu) Q[r * nu + i0 + 2 * e] = acc[e];
     }
     __syncthreads();
     // column pairs (c - 1, c) of row pairs (r0 + 2p, r0 + 2p + 1) as one float4;
@@ -216,7 +242,7 @@ cudaError_t launch_fdk_filter(const void *y, int y_dtype, int n_sel, int nu, int
                               double du, double dv, float *qt, cudaStream_t st) {
     if (n_sel <= 0) return cudaSuccess;
     const double m = sod / sdd;
-    const size_t smem = ((size_t)2 * FDK_ROWS * nu + nu / 2 + 1) * sizeof(float);
+    const size_t smem = ((size_t)FDK_ROWS * fr_row_len(nu) + (size_t)FDK_ROWS * nu + fr_kh(nu) + 1) * sizeof(float);
     dim3 grid((nv + FDK_ROWS - 1) / FDK_ROWS, n_sel);
     const double cu = 0.5 * (nu - 1), cv = 0.5 * (nv - 1);
     cudaError_t e = cudaSuccess;
