@@ -43,13 +43,12 @@ constexpr int FDK_VB = 32;     // views whose pair geometry a block forms at onc
 // even so that every column starts on a 16-byte boundary
 __host__ __device__ inline int fdk_row_stride(int nv) { return (nv + 5) & ~1; }
 
-// The filter's row staging: FR_PAD zero columns on each side of a row, and
-// one unused word after every 16 columns so that lanes 16 columns apart fall
-// in different shared-memory banks.
-constexpr int FR_PAD = 256;
+// The filter's row staging: FR_PAD zero columns on each side of a row and a
+// row stride of 2 (mod 32) words, so that the 32 lanes of a warp (8 rows x 2
+// column groups 16 apart x 2 parities) read 32 different shared-memory banks.
+constexpr int FR_PAD = 32;
 constexpr int FR_E = 8;  // outputs per thread: columns i0, i0 + 2, .., i0 + 14
-__device__ __forceinline__ int fr_addr(int c) { return c + (c >> 4); }
-__host__ __device__ inline int fr_row_len(int nu) { return (nu + 2 * FR_PAD - 1) + ((nu + 2 * FR_PAD - 1) >> 4) + 1; }
+__host__ __device__ inline int fr_row_len(int nu) { return ((nu + 2 * FR_PAD + 29) & ~31) + 2; }
 __host__ __device__ inline int fr_kh(int nu) { return (nu + FR_PAD + 2 * FR_E - 1) | 1; }  // odd
 
 template <typename TY>
@@ -79,37 +78,42 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
             const float w = sodf * rsqrtf(fmaf(a, a, fmaf(b, b, sod2)));
             val = w * to_f32(y[((size_t)s * nv + iv) * nu + iu]);
         }
-        P[r * rl + fr_addr(c)] = val;
+        P[r * rl + c] = val;
     }
     __syncthreads();
-    // A warp takes one row and 256 columns: lane l the 8 outputs i0 + 2e,
-    // i0 = Iw + 16 (l / 2) + l % 2.  Output i sums t h(n - i) P(n) over the odd
-    // offsets n - i (the even ones other than 0 vanish); with d = n - i0 the
-    // coefficient of output e is t h(d - 2e), so as d steps by 2 the 8
-    // coefficients shift by one place and one new one is read (the same for
-    // the whole warp).  d runs over [-Iw - 255, nu - 1 - Iw], which covers
-    // n = 0 .. nu - 1 for every lane; the zero padding supplies the rest.
+    // A warp takes the 8 rows and 32 columns [Iw, Iw + 32): lane l the row
+    // l / 4 and the 8 outputs i0 + 2e, i0 = Iw + 16 ((l / 2) % 2) + l % 2.
+    // Output i sums t h(n - i) P(n) over the odd offsets n - i (the even ones
+    // other than 0 vanish); with d = n - i0 the coefficient of output e is
+    // t h(d - 2e), so as d steps by 2 the 8 coefficients shift by one place and
+    // one new one is read (the same for the whole warp).  d runs over
+    // [-Iw - 31, nu - 1 - Iw], which covers n = 0 .. nu - 1 for every lane; the
+    // zero padding supplies the rest.
     const float c0 = (float)(1.0 / (4.0 * t));
-    const int nseg = (nu + 255) / 256;
+    const int nseg = (nu + 31) / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int task = warp; task < FDK_ROWS * nseg; task += FDK_FT / 32) {
-        const int r = task / nseg, Iw = (task - r * nseg) * 256;
-        const int i0 = Iw + 16 * (lane >> 1) + (lane & 1);
-        const float *Pr = P + r * rl;
+    const int r = lane >> 2;
+    const float *Pr = P + r * rl + FR_PAD;
+    for (int seg = warp; seg < nseg; seg += FDK_FT / 32) {
+        const int Iw = seg * 32;
+        const int i0 = Iw + 16 * ((lane >> 1) & 1) + (lane & 1);
         float acc[FR_E], hw[FR_E];
-        const int dmin = -Iw - 255, dmax = nu - 1 - Iw;
+        const int dmin = -Iw - 31, dmax = nu - 1 - Iw;
 #pragma unroll
         for (int e = 0; e < FR_E; ++e) {
-            acc[e] = c0 * Pr[fr_addr(i0 + 2 * e + FR_PAD)];
+            acc[e] = c0 * Pr[i0 + 2 * e];
             hw[e] = H[(dmin - 2 * e + KH) >> 1];
         }
-        for (int d = dmin; d <= dmax; d += 2) {
-            const float p = Pr[fr_addr(i0 + d + FR_PAD)];
+        const float *pp = Pr + i0;
+        const float *hh = H + ((dmin + 2 + KH) >> 1);
+#pragma unroll 8
+        for (int d = dmin; d <= dmax; d += 2, ++hh) {
+            const float p = pp[d];
 #pragma unroll
             for (int e = 0; e < FR_E; ++e) acc[e] = fmaf(hw[e], p, acc[e]);
 #pragma unroll
             for (int e = FR_E - 1; e > 0; --e) hw[e] = hw[e - 1];
-            hw[0] = H[(d + 2 + KH) >> 1];
+            hw[0] = *hh;
         }
 #pragma unroll
         for (int e = 0; e < FR_E; ++e)
