@@ -62,9 +62,12 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
     float *H = Q + FDK_ROWS * nu;        // t h(k t) for odd k in [-KH, KH], at (k + KH) / 2
     const int s = blockIdx.y, r0 = blockIdx.x * FDK_ROWS;
     const double t = du_m;
+    // the odd taps in FP32 (k^2 is exact, one rounded division): FP64
+    // divisions per block would cost more than the filtering
+    const float ct = (float)(-1.0 / (M_PI * M_PI * t));
     for (int j = threadIdx.x; j <= KH; j += FDK_FT) {
-        const double k = 2.0 * j - KH;
-        H[j] = (float)(-1.0 / (M_PI * M_PI * k * k * t));
+        const float k = (float)(2 * j - KH);
+        H[j] = ct / (k * k);
     }
     // cosine weight in FP32 (relative error below 1e-6): FP64 arithmetic is
     // slow on this part
