@@ -18,6 +18,10 @@ design notes):
     from SplitMix64; a short last slice is padded from the front of the
     same permutation;
   * the prox of mu||.||_1 + indicator{x >= 0} is max(v - alpha mu, 0).
+
+Params.reg / x_max / tv_iters / tv_warm select the other regularisers of
+oracle/tv.py (the box-constrained l1 and isotropic TV); the defaults are the
+paper's R.
 """
 from __future__ import annotations
 
@@ -28,6 +32,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 from . import backproject, project
+from . import tv as tv_oracle
 
 MASK64 = (1 << 64) - 1
 GAMMA = 0x9E3779B97F4A7C15          # SplitMix64 increment (Steele, Lea & Flood, 2014)
@@ -114,6 +119,30 @@ class Params:
     max_backtracks: int = 60
     seed: int = 0
     fixed_step: bool = False  # forward-backward with the constant step alpha0, no test (2.3)
+    reg: str = "l1"           # "l1": mu||x||_1, "tv": mu TV(x); either with the box [0, x_max]
+    x_max: float = math.inf
+    tv_iters: int = 20        # FGP iterations per prox ("tv")
+    tv_warm: bool = True      # each TV prox starts from the dual the previous one ended with
+
+
+class TVState:
+    """The dual field carried from one TV prox to the next (warm start)."""
+
+    def __init__(self):
+        self.q = None
+
+
+def reg_prox(v: np.ndarray, alpha: float, p: Params, tv_state: Optional[TVState] = None) -> np.ndarray:
+    """prox_{alpha R}(v) for the regulariser p.reg (oracle/tv.py)."""
+    if p.reg == "l1":
+        return tv_oracle.prox_l1_box(v, alpha, p.mu, p.x_max)
+    if p.reg != "tv":
+        raise ValueError("unknown regulariser %r" % p.reg)
+    q0 = tv_state.q if (p.tv_warm and tv_state is not None) else None
+    x, q = tv_oracle.prox_tv(v, alpha * p.mu, p.tv_iters, p.x_max, q0=q0)
+    if p.tv_warm and tv_state is not None:
+        tv_state.q = q
+    return x
 
 
 @dataclasses.dataclass
@@ -151,7 +180,7 @@ class LineSearchError(RuntimeError):
 
 def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
             alpha_init: Optional[float] = None, replay_alpha: Optional[float] = None,
-            k: int = 0, epoch: int = 0):
+            k: int = 0, epoch: int = 0, tv_state: Optional[TVState] = None):
     """One iteration of Alg. 1, Steps 2b-2d, on the mini-batch ``views``.
 
     Returns (x_next, StepRecord).  With ``replay_alpha`` the step size is
@@ -173,7 +202,7 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
     if p.fixed_step:
         # the deterministic FB baseline of Sec. 3 (with the full batch): one
         # forward-backward step at the constant alpha_0, no sufficient-decrease test
-        xbar = prox(x - p.alpha0 * g, p.alpha0, p.mu)
+        xbar = reg_prox(x - p.alpha0 * g, p.alpha0, p, tv_state)
         d = xbar - x
         t = Trial(p.alpha0, float("nan"), float(np.dot(g.ravel(), d.ravel())),
                   float(np.dot(d.ravel(), d.ravel())), float("nan"), float("nan"), True)
@@ -181,7 +210,7 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
     trials = []
     for bt in range(p.max_backtracks + 1):
         # Step 2c: forward-backward point and the test (2.3)
-        xbar = prox(x - alpha * g, alpha, p.mu)
+        xbar = reg_prox(x - alpha * g, alpha, p, tv_state)
         d = xbar - x
         gTd = float(np.dot(g.ravel(), d.ravel()))
         dd = float(np.dot(d.ravel(), d.ravel()))
@@ -210,13 +239,14 @@ def run(geom, b: np.ndarray, x0: np.ndarray, p: Params, epochs: int,
     x = np.asarray(x0, dtype=np.float64).reshape(geom.vol_shape).copy()
     records = []
     k = 0
+    tv_state = TVState()
     for t, (N_t, iters) in enumerate(schedule(n_theta, p.N0, n_max, p.C, p.eps_base, epochs),
                                      start=1):
         for views in epoch_batches(p.seed, t, n_theta, N_t):
             if max_iters is not None and k >= max_iters:
                 return x, records
             ra = None if replay is None else replay[k]
-            x, rec = fb_step(geom, x, b, views, p, replay_alpha=ra, k=k, epoch=t)
+            x, rec = fb_step(geom, x, b, views, p, replay_alpha=ra, k=k, epoch=t, tv_state=tv_state)
             records.append(rec)
             k += 1
     return x, records
