@@ -86,6 +86,17 @@ typedef struct {
     double du, dv;            /* detector pixel size */
 } fbl_geometry_desc;
 
+/* The regulariser R of eq. (2.1).  FB-LISA allows any proper convex lower
+ * semicontinuous R whose prox is computable (Sec. 2.1); the paper runs the l1
+ * one.  Both choices here include the box 0 <= x <= x_max (x_max = +inf: the
+ * paper's nonnegativity). */
+typedef enum {
+    FBL_REG_L1 = 0,   /* R = mu ||x||_1 + box; prox min(max(v - alpha mu, 0), x_max) */
+    FBL_REG_TV = 1    /* R = mu TV(x) + box, TV isotropic with forward differences (zero at
+                         each axis's last index, unit grid spacing); prox by FGP iterations
+                         on the dual (see prox_tv) */
+} fbl_reg;
+
 /* Hyperparameters of Algorithm 1 (names as in the paper, Sec. 2.2 and Sec. 3). */
 typedef struct {
     double alpha0;            /* initial step alpha_0 (Sec. 3: 1e-3) */
@@ -110,6 +121,11 @@ typedef struct {
                                  N0 = n_max = n_views): no trial objective is evaluated,
                                  f_xbar and margin are reported as NaN; use_graph and
                                  proposal are ignored */
+    int32_t reg;              /* fbl_reg; FBL_REG_TV needs use_graph 0 and no batch */
+    int32_t tv_iters;         /* FGP iterations per TV prox (each trial of the line search) */
+    int32_t tv_warm;          /* 1: each TV prox starts from the dual the previous one ended
+                                 with (across trials and iterations); 0: from zero */
+    double x_max;             /* upper bound of the box in R (+inf: none, the paper's R) */
 } fbl_params;
 
 /* Record of one iteration of Algorithm 1. */
@@ -135,7 +151,8 @@ typedef struct {
 
 /* Defaults: alpha0 1e-3, beta 0.5, mu 1, C 1, eps_base 0.99, N0 8, n_max 0,
  * max_backtracks 60, proposal 0, seed 0, F32 storage, no graph, no hook,
- * no autotuning, line search on (fixed_step 0). */
+ * no autotuning, line search on (fixed_step 0), reg FBL_REG_L1, tv_iters 20,
+ * tv_warm 1, x_max +inf. */
 FBL_API void fbl_params_default(fbl_params *p);
 
 /*
@@ -250,6 +267,37 @@ FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, i
 FBL_API fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtype, const void *b,
                             int32_t b_dtype, double mu, const void *x_true, double *out3_host,
                             void *stream);
+
+/*
+ * prox_tv -- the prox of the TV regulariser (FBL_REG_TV) on one volume:
+ *     x = argmin_{0 <= z <= x_max} 1/2 ||z - v||^2 + lambda TV(z),
+ * TV(z) = sum over voxels of the Euclidean norm of the forward differences
+ * along x, y and z (a zero difference at each axis's last index).  The paper
+ * has no counterpart: FB-LISA admits any convex R with a computable prox
+ * (Sec. 2.1), and this one has no closed form.  It runs `iters` iterations of
+ * the fast gradient projection on the dual (Beck and Teboulle, 2009): with a
+ * dual field q of unit vectors, x(q) = clip(v - lambda K^T q, 0, x_max), step
+ * q <- P_ball(r + K x(r) / (12 lambda)) with momentum r from the sequence
+ * t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, starting from q (q_in = 1,
+ * a warm start; components without a difference are zeroed) or from zero;
+ * x = x(q) of the last q.  lambda = 0 gives clip(v, 0, x_max).
+ * dims = {nx, ny, nz}; v, x: [nz][ny][nx] float32, x must not alias v;
+ * q: NULL, or 3 * nx*ny*nz float32 [3][nz][ny][nx] (components along x, y, z),
+ * read when q_in = 1 and holding the last dual on return.  Host or device
+ * pointers (host ones are staged).  Needs ny, nz <= 65535, lambda >= 0,
+ * x_max > 0 (+inf allowed), 0 <= iters <= 100000: else FBL_E_INVAL.  FP32
+ * arithmetic.  Device scratch of 4 volumes, stream-ordered.  Synchronous with
+ * host buffers, else asynchronous on `stream`.
+ */
+FBL_API fbl_status prox_tv(const int32_t dims[3], const float *v, double lambda, double x_max, int32_t iters,
+                           float *q, int32_t q_in, float *x, void *stream);
+
+/*
+ * tv_norm -- TV(x) as prox_tv defines it, an FP64 sum of FP32 per-voxel norms
+ * in a fixed order.  dims = {nx, ny, nz}, x [nz][ny][nx] float32 (host or
+ * device); *out_host receives the value.  Synchronous.
+ */
+FBL_API fbl_status tv_norm(const int32_t dims[3], const float *x, double *out_host, void *stream);
 
 /*
  * prox_reduce_static -- the same computation and outputs as prox_reduce, for

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfblisa.so")
 
 F32, BF16, F16 = 0, 1, 2
+REG_L1, REG_TV = 0, 1
 STATUS = {0: "FBL_OK", 1: "FBL_E_INVAL", 2: "FBL_E_NOMEM", 3: "FBL_E_CUDA",
           4: "FBL_E_UNSUPPORTED", 5: "FBL_E_LINESEARCH", 6: "FBL_E_NONFINITE", 7: "FBL_E_TIMEOUT"}
 
@@ -45,7 +46,8 @@ class fbl_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("x_dtype", ctypes.c_int32),
                 ("b_dtype", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("force_reject", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("fixed_step", ctypes.c_int32)]
+                ("fixed_step", ctypes.c_int32), ("reg", ctypes.c_int32), ("tv_iters", ctypes.c_int32),
+                ("tv_warm", ctypes.c_int32), ("x_max", ctypes.c_double)]
 
 
 class fbl_step_stats(ctypes.Structure):
@@ -84,7 +86,7 @@ EXPORTS = ["fbl_params_default", "fblisa_profile", "geometry_create", "geometry_
            "geometry_set_launch", "evaluate", "mlp_forward", "mlp_gradient", "mlp_train",
            "fblisa_set_proposal", "fblisa_batch_create", "fblisa_batch_destroy",
            "fblisa_batch_set_proposal", "fblisa_batch_step", "fblisa_batch_run",
-           "fblisa_batch_info", "fblisa_batch_last_batch", "fdk"]
+           "fblisa_batch_info", "fblisa_batch_last_batch", "fdk", "prox_tv", "tv_norm"]
 
 
 def _load():
@@ -124,6 +126,8 @@ def _load():
         "fblisa_batch_info": (st, [vp, P(i32), P(i64)]),
         "fblisa_batch_last_batch": (st, [vp, i32, P(i32), i32, P(i32)]),
         "fdk": (st, [vp, vp, i32, P(i32), i32, vp, vp]),
+        "prox_tv": (st, [P(i32), vp, dbl, dbl, i32, vp, i32, vp, vp]),
+        "tv_norm": (st, [P(i32), vp, P(dbl), vp]),
         "fbl_last_error": (ctypes.c_char_p, []),
         "fbl_schedule": (st, [i32, i32, i32, dbl, dbl, i32, P(i32), P(i32)]),
         "fbl_epoch_batches": (st, [ctypes.c_uint64, i32, i32, i32, P(i32)]),
@@ -334,6 +338,33 @@ def prox_reduce_static(x, g, alpha: float, mu: float, xbar, stream=None):
     _check(lib.prox_reduce_static(_ptr(x), _dtype_code(x), _ptr(g), n, float(alpha), float(mu),
                                   _ptr(xbar), out, _stream(x, g, xbar, stream=stream)))
     return xbar, (out[0], out[1], out[2])
+
+
+def prox_tv(v, lam: float, iters: int, x_max: float = float("inf"), q=None, q_in: bool = False, x=None,
+            stream=None):
+    """prox of lam TV + indicator{0 <= x <= x_max} at v [nz][ny][nx] float32 by
+    ``iters`` FGP iterations; q [3][nz][ny][nx] float32: the start (q_in) and
+    the last dual on return.  Returns x."""
+    if _dtype_code(v) != F32 or (x is not None and _dtype_code(x) != F32) or (q is not None and _dtype_code(q) != F32):
+        raise TypeError("prox_tv works on float32 volumes")
+    nz, ny, nx = (int(t) for t in v.shape)
+    if x is None:
+        x = _like(v, (nz, ny, nx), F32)
+    dims = (ctypes.c_int32 * 3)(nx, ny, nz)
+    _check(lib.prox_tv(dims, _ptr(v), float(lam), float(x_max), int(iters), _ptr(q) if q is not None else None,
+                       1 if q_in else 0, _ptr(x), _stream(v, x, stream=stream)))
+    return x
+
+
+def tv_norm(x, stream=None) -> float:
+    """Isotropic TV of x [nz][ny][nx] float32 (forward differences, FP64 sum)."""
+    if _dtype_code(x) != F32:
+        raise TypeError("tv_norm works on float32 volumes")
+    nz, ny, nx = (int(t) for t in x.shape)
+    dims = (ctypes.c_int32 * 3)(nx, ny, nz)
+    out = ctypes.c_double()
+    _check(lib.tv_norm(dims, _ptr(x), ctypes.byref(out), _stream(x, stream=stream)))
+    return out.value
 
 
 MLP_PARAMS = 4801

@@ -145,6 +145,10 @@ extern "C" void fbl_params_default(fbl_params *p) {
     p->b_dtype = FBL_F32;
     p->use_graph = 0;
     p->force_reject = 0;
+    p->reg = FBL_REG_L1;
+    p->tv_iters = 20;
+    p->tv_warm = 1;
+    p->x_max = INFINITY;
 }
 
 extern "C" fbl_status geometry_create(const fbl_geometry_desc *desc, fbl_geometry **out) {
@@ -783,6 +787,61 @@ extern "C" fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g
     return FBL_OK;
 }
 
+extern "C" fbl_status prox_tv(const int32_t dims[3], const float *v, double lambda, double x_max, int32_t iters,
+                              float *q, int32_t q_in, float *x, void *stream) {
+    if (!dims || !v || !x || (q_in && !q)) return fail(FBL_E_INVAL, "prox_tv: null argument");
+    const int nx = dims[0], ny = dims[1], nz = dims[2];
+    if (!tv_dims_ok(nx, ny, nz)) return fail(FBL_E_INVAL, "prox_tv: need dims > 0 and ny, nz <= 65535");
+    if (!(lambda >= 0) || !std::isfinite(lambda) || !(x_max > 0) || iters < 0 || iters > 100000)
+        return fail(FBL_E_INVAL, "prox_tv: need lambda >= 0, x_max > 0, 0 <= iters <= 100000");
+    if ((const void *)x == (const void *)v) return fail(FBL_E_INVAL, "prox_tv: x must not alias v");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)nx * ny * nz;
+    AsyncBuf vs, scratch, xs;
+    const void *vd = nullptr;
+    fbl_status st;
+    if ((st = device_input(v, n * sizeof(float), vs, &vd, s))) return st;
+    // q (3 volumes, unless the caller's device q is used), r (3), y (1)
+    const bool q_dev = q && is_device_ptr(q);
+    CK(scratch.alloc((q_dev ? 4 : 7) * n * sizeof(float), s), "scratch");
+    float *r = (float *)scratch.p, *y = r + 3 * n;
+    float *qd = q_dev ? q : y + n;
+    if (q && !q_dev && q_in) CK(cudaMemcpyAsync(qd, q, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s), "q H2D");
+    const bool x_dev = is_device_ptr(x);
+    float *xd = x;
+    if (!x_dev) {
+        CK(xs.alloc(n * sizeof(float), s), "output staging");
+        xd = (float *)xs.p;
+    }
+    CK(launch_tv_prox((const float *)vd, nx, ny, nz, (float)lambda, (float)x_max, iters, q_in ? 1 : 0, qd, r, y,
+                      xd, s),
+       "TV prox kernels");
+    if (q && !q_dev) CK(cudaMemcpyAsync(q, qd, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s), "q D2H");
+    if (!x_dev) CK(cudaMemcpyAsync(x, xd, n * sizeof(float), cudaMemcpyDeviceToHost, s), "x D2H");
+    if (!x_dev || (q && !q_dev) || !is_device_ptr(v)) CK(cudaStreamSynchronize(s), "prox_tv");
+    return FBL_OK;
+}
+
+extern "C" fbl_status tv_norm(const int32_t dims[3], const float *x, double *out_host, void *stream) {
+    if (!dims || !x || !out_host) return fail(FBL_E_INVAL, "tv_norm: null argument");
+    const int nx = dims[0], ny = dims[1], nz = dims[2];
+    if (!tv_dims_ok(nx, ny, nz)) return fail(FBL_E_INVAL, "tv_norm: need dims > 0 and ny, nz <= 65535");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)nx * ny * nz;
+    AsyncBuf xs, part, res;
+    const void *xd = nullptr;
+    fbl_status st;
+    if ((st = device_input(x, n * sizeof(float), xs, &xd, s))) return st;
+    const int np = tv_norm_num_partials(nx, ny, nz);
+    CK(part.alloc((size_t)np * sizeof(double), s), "partials");
+    CK(res.alloc(sizeof(double), s), "result");
+    CK(launch_tv_norm((const float *)xd, nx, ny, nz, (double *)part.p, s), "TV norm kernel");
+    CK(launch_reduce((const double *)part.p, np, np, 1, (double *)res.p, s), "reduce");
+    CK(cudaMemcpyAsync(out_host, res.p, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+    CK(cudaStreamSynchronize(s), "tv_norm");
+    return FBL_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Solver: Algorithm 1
 // ---------------------------------------------------------------------------
@@ -839,14 +898,36 @@ struct fbl_solver {
     PropState *h_ps = nullptr;                    // pinned mirror (host-loop mode)
     float *d_mlp = nullptr;                       // network parameters, NULL until set
     float margin = 0.25f;
+    // TV prox (reg = FBL_REG_TV): b, y, q[3], r[3] as consecutive FP32 volumes
+    float *tv_buf = nullptr;
+    bool tv_have_q = false;                       // q holds the previous prox's dual
 };
 
 namespace {
+
+// Step 2c's forward-backward point x_bar = prox_{alpha R}(x - alpha g) into
+// s->tr, with the partial sums of (2.3): the l1 prox (with the box), or the
+// TV prox by FGP iterations from the previous call's dual.
+cudaError_t solver_prox(fbl_solver *s, double alpha, int *npp, cudaStream_t st) {
+    const int xdt = s->p.x_dtype;
+    if (s->p.reg != FBL_REG_TV)
+        return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu), (float)s->p.x_max,
+                              s->tr, xdt, s->partials, npp, st);
+    const size_t n = (size_t)s->L.nx * s->L.ny * s->L.nz;
+    float *b = s->tv_buf, *y = b + n, *q = y + n, *r = q + 3 * n;
+    const int warm = s->p.tv_warm && s->tv_have_q;
+    cudaError_t e = launch_tv_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu),
+                                      (float)s->p.x_max, s->p.tv_iters, warm, b, q, r, y, s->tr, xdt, s->partials,
+                                      npp, st);
+    if (e == cudaSuccess) s->tv_have_q = true;
+    return e;
+}
 
 void solver_free(fbl_solver *s) {
     cudaFree(s->st);
     cudaFree(s->tr);
     cudaFree(s->grad);
+    cudaFree(s->tv_buf);
     cudaFree(s->rt);
     cudaFree(s->bstage);
     cudaFree(s->xstage);
@@ -1088,11 +1169,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, nbp, nbp, 1, s->d_sc + 5, st); }),
            "reduce");
         const double alpha = s->p.alpha0;
-        CK(prof_launch(s, 3, st, [&] {
-               return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu), s->tr, xdt,
-                                     s->partials, &npp, st);
-           }),
-           "prox kernel");
+        CK(prof_launch(s, 3, st, [&] { return solver_prox(s, alpha, &npp, st); }), "prox kernel");
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
            "reduce");
         CK(cudaMemcpyAsync(s->h_sc, s->d_sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
@@ -1153,6 +1230,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         cfg.alpha_init = s->p.alpha0;
         cfg.beta = s->p.beta;
         cfg.mu = s->p.mu;
+        cfg.x_max = s->p.x_max;
         cfg.scale = scale;
         cfg.max_backtracks = s->p.max_backtracks;
         cfg.force_reject = s->p.force_reject;
@@ -1229,6 +1307,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         cfg.alpha_init = s->p.alpha0;
         cfg.beta = s->p.beta;
         cfg.mu = s->p.mu;
+        cfg.x_max = s->p.x_max;
         cfg.scale = scale;
         cfg.max_backtracks = s->p.max_backtracks;
         cfg.N_t = N;
@@ -1253,11 +1332,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     double rho0 = 0, rho1 = 0, gTd = 0, dd = 0, f_x = 0, f_xb = 0, rhs = 0;
     for (bt = 0; bt <= s->p.max_backtracks; ++bt) {
         int npp = 0;
-        CK(prof_launch(s, 3, st, [&] {
-               return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu),
-                                     s->tr, xdt, s->partials, &npp, st);
-           }),
-           "prox kernel");
+        CK(prof_launch(s, 3, st, [&] { return solver_prox(s, alpha, &npp, st); }), "prox kernel");
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, npp, npp, 3, s->d_sc + 1, st); }),
            "reduce");
         CK(prof_launch(s, 1, st, [&] {
@@ -1576,6 +1651,15 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
         return fail(FBL_E_INVAL, "fblisa_create: need 1 <= N0 <= n_max <= n_views");
     if (p->proposal != 0 && p->proposal != 1) return fail(FBL_E_INVAL, "fblisa_create: proposal must be 0 or 1");
     if (p->fixed_step != 0 && p->fixed_step != 1) return fail(FBL_E_INVAL, "fblisa_create: fixed_step must be 0 or 1");
+    if (p->reg != FBL_REG_L1 && p->reg != FBL_REG_TV) return fail(FBL_E_INVAL, "fblisa_create: reg must be 0 or 1");
+    if (!(p->x_max > 0.0)) return fail(FBL_E_INVAL, "fblisa_create: need x_max > 0 (+inf: no upper bound)");
+    if (p->reg == FBL_REG_TV) {
+        if (p->tv_iters < 0 || p->tv_iters > 100000 || (p->tv_warm != 0 && p->tv_warm != 1))
+            return fail(FBL_E_INVAL, "fblisa_create: need 0 <= tv_iters <= 100000 and tv_warm 0 or 1");
+        if (p->use_graph)
+            return fail(FBL_E_UNSUPPORTED, "fblisa_create: the TV prox runs in host-loop mode (use_graph 0)");
+        if (!tv_dims_ok(d.nz, d.nx, d.ny)) return fail(FBL_E_UNSUPPORTED, "fblisa_create: volume too large for TV");
+    }
     auto s = new fbl_solver();
     s->g = g;
     s->dg = g->dg;
@@ -1593,6 +1677,10 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
         if (e == cudaSuccess) e = cudaMemset(*vols[q], 0, s->vol_bytes);  // zero border, once
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, nvox * sizeof(float));
+    if (e == cudaSuccess && p->reg == FBL_REG_TV) {
+        // b, y and the dual pair (q, r) of the TV prox: 8 volumes of FP32
+        e = cudaMalloc(&s->tv_buf, 8 * nvox * sizeof(float));
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->xstage, nvox * es);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_views, (size_t)d.n_views * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_sc, 8 * sizeof(double));
@@ -1952,6 +2040,7 @@ fbl_status batch_iterate(fbl_batch *bt, const void *const *b, const char *b_dev,
         cfg.alpha_init = s->p.alpha0;
         cfg.beta = s->p.beta;
         cfg.mu = s->p.mu;
+        cfg.x_max = s->p.x_max;
         cfg.scale = (double)d.n_views / (double)N;
         cfg.max_backtracks = s->p.max_backtracks;
         cfg.force_reject = s->p.force_reject;
@@ -2041,6 +2130,8 @@ extern "C" fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, cons
             return fail(FBL_E_INVAL, "fblisa_batch_create: every volume needs the same x_dtype and b_dtype");
         if (params[v].fixed_step)
             return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: the batch runs the line search (fixed_step 0)");
+        if (params[v].reg != FBL_REG_L1)
+            return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: the batch runs the l1 prox (reg 0)");
     }
     if (params[0].b_dtype != params[0].x_dtype)
         return fail(FBL_E_UNSUPPORTED, "fblisa_batch_create: b_dtype must equal x_dtype");

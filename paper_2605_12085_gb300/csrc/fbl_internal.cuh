@@ -164,13 +164,29 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
                                double *g2_partials = nullptr);
 int backproject_num_partials(const DevGeom &g);
 
-// x_bar = max(x - alpha*g - alpha*mu, 0) on the solver's state: reads vol
-// (current x) and gzi, writes trial; partials[3][nblk] =
+// x_bar = min(max(x - alpha*g - alpha*mu, 0), xmax) on the solver's state:
+// reads vol (current x) and gzi, writes trial; partials[3][nblk] =
 // (g^T d, d^T d, |x_bar|_1) per block.
-cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu,
+cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu, float xmax,
                            void *trial, int dtype, double *partials, int *n_partials,
                            cudaStream_t st);
 int prox_zi_num_partials(int nx, int ny, int nz);
+
+// Total variation (k_tv.cu).  Volumes in a memory order (n0 fastest, n1, n2),
+// dual fields as 3 such volumes.  tv_prox: x = prox of lam TV + indicator of
+// [0, xmax] at v by `iters` FGP iterations, from q (q_in) or zero; q ends as
+// the last dual; r and y are scratch (3 volumes, 1 volume).
+bool tv_dims_ok(int n0, int n1, int n2);
+cudaError_t launch_tv_prox(const float *v, int n0, int n1, int n2, float lam, float xmax, int iters, int q_in,
+                           float *q, float *r, float *y, float *x, cudaStream_t st);
+int tv_norm_num_partials(int n0, int n1, int n2);
+cudaError_t launch_tv_norm(const float *x, int n0, int n1, int n2, double *partials, cudaStream_t st);
+// The solver's TV trial point: b = x - alpha g ([j][i][k]), FGP from q
+// (warm) or zero, then x_bar = P_C(b - lam K^T q) into trial with the three
+// partial sums of launch_prox_zi (same block count).
+cudaError_t launch_tv_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float lam, float xmax,
+                              int iters, int warm, float *b, float *q, float *r, float *y, void *trial, int dtype,
+                              double *partials, int *n_partials, cudaStream_t st);
 
 // Flat prox on n elements (public prox_reduce).
 cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float alpha, float amu,
@@ -204,6 +220,7 @@ cudaError_t launch_mlp_train(float *params, float *adam_m, float *adam_v, const 
 // Line-search state of one iteration (device memory).
 struct LSState {
     double alpha_init, alpha, beta, mu, scale;  // scale = n_theta / N_t
+    double x_max;               // upper bound of the box in R (+inf: none)
     double rho0, gTd, dd, rho1, f_x, f_xbar, rhs, g2;
     int trials, max_backtracks, accepted, status, force_reject;
     int j_start;                // first trial = alpha0 * beta^j_start

@@ -219,7 +219,7 @@ __device__ __forceinline__ void prox_tile(const T *__restrict__ vol, const ZLayo
                                           T *__restrict__ trial, double *__restrict__ partials,
                                           int blk, int nblk) {
     const double a = ls->alpha;
-    const float alpha = (float)a, amu = (float)(a * ls->mu);
+    const float alpha = (float)a, amu = (float)(a * ls->mu), xmax = (float)ls->x_max;
     const int row = blk * PZ_TY + threadIdx.y;
     float sums[3] = {0.f, 0.f, 0.f};
     if (row < L.nx * L.ny) {
@@ -231,7 +231,7 @@ __device__ __forceinline__ void prox_tile(const T *__restrict__ vol, const ZLayo
         for (int k = threadIdx.x; k < L.nz; k += PZ_TX) {
             const float x = to_f32(src[k]);
             const float gg = gr[k];
-            const float xb = fmaxf(fmaf(-alpha, gg, x) - amu, 0.f);
+            const float xb = fminf(fmaxf(fmaf(-alpha, gg, x) - amu, 0.f), xmax);
             const T xs = from_f32<T>(xb);
             const float xr = to_f32(xs);
             dst[k] = xs;

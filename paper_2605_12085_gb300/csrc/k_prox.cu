@@ -1,6 +1,7 @@
 // K3 -- the forward-backward point of Step 2c of Algorithm 1,
-//     x_bar = prox_{alpha R}(x - alpha g) = max(x - alpha g - alpha mu, 0),
-// R = mu||.||_1 + indicator{x >= 0} (eq. (2.1)), fused with the reductions the
+//     x_bar = prox_{alpha R}(x - alpha g) = min(max(x - alpha g - alpha mu, 0), x_max),
+// R = mu||.||_1 + indicator{0 <= x <= x_max} (eq. (2.1) with x_max = +inf, the
+// paper's R; a finite x_max adds the box), fused with the reductions the
 // test (2.3) needs: g^T (x_bar - x), ||x_bar - x||^2 (and ||x_bar||_1 for the
 // objective F), all taken over the stored (rounded) x_bar.  Memory-bound:
 // per voxel it reads x and g once and writes x_bar once, in the z-innermost
@@ -92,7 +93,7 @@ constexpr int PZ_TY = 4;
 template <typename T>
 __global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi(const T *__restrict__ vol, ZLayout L,
                                                           const float *__restrict__ gzi, float alpha,
-                                                          float amu, T *__restrict__ trial,
+                                                          float amu, float xmax, T *__restrict__ trial,
                                                           double *__restrict__ partials) {
     const int row = blockIdx.x * PZ_TY + threadIdx.y;
     float sums[3] = {0.f, 0.f, 0.f};
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(PZ_TX *PZ_TY) k_prox_zi(const T *__restrict__ 
         for (int k = threadIdx.x; k < L.nz; k += PZ_TX) {
             const float x = to_f32(src[k]);
             const float gg = gr[k];
-            const float xb = fmaxf(fmaf(-alpha, gg, x) - amu, 0.f);
+            const float xb = fminf(fmaxf(fmaf(-alpha, gg, x) - amu, 0.f), xmax);
             const T xs = from_f32<T>(xb);
             const float xr = to_f32(xs);
             dst[k] = xs;
@@ -265,7 +266,7 @@ int prox_zi_num_partials(int nx, int ny, int nz) {
     return (nx * ny + PZ_TY - 1) / PZ_TY;
 }
 
-cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu,
+cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float amu, float xmax,
                            void *trial, int dtype, double *partials, int *n_partials,
                            cudaStream_t st) {
     const int nb = prox_zi_num_partials(L.nx, L.ny, L.nz);
@@ -273,15 +274,15 @@ cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float a
     dim3 block(PZ_TX, PZ_TY);
     switch (dtype) {
         case FBL_BF16:
-            k_prox_zi<<<nb, block, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, alpha, amu,
+            k_prox_zi<<<nb, block, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, alpha, amu, xmax,
                                             (__nv_bfloat16 *)trial, partials);
             break;
         case FBL_F16:
-            k_prox_zi<<<nb, block, 0, st>>>((const __half *)vol, L, gzi, alpha, amu, (__half *)trial,
+            k_prox_zi<<<nb, block, 0, st>>>((const __half *)vol, L, gzi, alpha, amu, xmax, (__half *)trial,
                                             partials);
             break;
         default:
-            k_prox_zi<<<nb, block, 0, st>>>((const float *)vol, L, gzi, alpha, amu, (float *)trial,
+            k_prox_zi<<<nb, block, 0, st>>>((const float *)vol, L, gzi, alpha, amu, xmax, (float *)trial,
                                             partials);
             break;
     }
