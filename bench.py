@@ -464,6 +464,61 @@ def fdk_record(fbl, G, g, b, xt, device, reps=2):
             "rel_error_vs_phantom": re}
 
 
+def regularisers_record(fbl, G, g, b, xt, device, peaks, iters=4):
+    """The other regularisers at the workload's size: prox_tv alone (20 FGP
+    iterations on a volume, its algorithmic HBM bytes: 24 B/voxel to start the
+    dual, 72 B/voxel per iteration (20 for y = P_C(b - lam K^T r), 52 for the
+    dual step), 20 B/voxel for the result) against the measured copy
+    bandwidth; and FB-LISA iterations with R = mu||x||_1 + box and with
+    R = mu TV + box (10 FGP iterations per prox), ms per iteration from CUDA
+    events, beside the paper's R."""
+    import torch
+    stream = torch.cuda.current_stream(device)
+    n = g.n_vox
+    v = torch.from_numpy(xt).to(device)
+    q = torch.zeros((3,) + tuple(v.shape), dtype=torch.float32, device=device)
+    xo = torch.empty_like(v)
+    fgp = 20
+    for _ in range(2):
+        fbl.prox_tv(v, 0.01, fgp, q=q, x=xo)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        fbl.prox_tv(v, 0.01, fgp, q=q, x=xo)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / reps
+    byt = float(n) * (24 + 72 * fgp + 20)
+    gbs = byt / (ms * 1e-3) / 1e9
+    tv_x = fbl.tv_norm(v)
+    del q, xo
+    out = {"prox_tv": {"voxels": n, "fgp_iterations": fgp, "ms": ms, "algorithmic_bytes": byt,
+                       "achieved_gbs": gbs, "peak_gbs": peaks.get("hbm_gbs"),
+                       "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
+           "tv_of_phantom": tv_x}
+    x_max = 1.0
+    runs = {"l1": {}, "l1_box": {"x_max": x_max}, "tv_box": {"reg": fbl.REG_TV, "tv_iters": 10, "x_max": x_max}}
+    wl_mu = 0.02
+    for name, kw in runs.items():
+        S = fbl.fblisa_create(G, fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl_mu, N0=40, seed=3003, **kw))
+        x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+        S.step(x, b)
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        st = [S.step(x, b) for _ in range(iters)]
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        out[name] = {"ms_per_iteration": e0.elapsed_time(e1) / iters,
+                     "backtracks_per_iteration": sum(t["backtracks"] for t in st) / iters,
+                     "max_x": float(x.max()), "tv_x": fbl.tv_norm(x)}
+        del S, x
+    out["mu"] = wl_mu
+    return out
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -798,6 +853,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         out["full_sweep"] = full_sweep(fbl, G, g, x, device)
         out["fdk"] = fdk_record(fbl, G, g, b, xt, device)
+        out["regularisers"] = regularisers_record(fbl, G, g, b, xt, device, peaks)
 
     # storage-precision variants (BF16 / FP16 iterates and data, FP32 arithmetic)
     if args.variants:
