@@ -11,7 +11,9 @@ Contents:
     plain C double precision (``joseph.c``);
   * ``fblisa`` -- Algorithm 1 (FB-LISA) step by step in numpy float64;
   * ``fdk`` -- the FDK reconstruction (cosine weighting, Ram-Lak filter,
-    weighted backprojection) in numpy float64.
+    weighted backprojection) in numpy float64;
+  * ``tv`` -- other regularisers: the box-constrained l1 prox and the
+    isotropic TV prox by FGP iterations on the dual, in numpy float64.
 
 Pins (checks against facts the paper and mathematics fix, not against this
 code) live in ``tests/test_oracle_*.py``.  One function is "parity unpinned"
