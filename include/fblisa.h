@@ -286,7 +286,8 @@ FBL_API fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtyp
  * read when q_in = 1 and holding the last dual on return.  Host or device
  * pointers (host ones are staged).  Needs ny, nz <= 65535, lambda >= 0,
  * x_max > 0 (+inf allowed), 0 <= iters <= 100000: else FBL_E_INVAL.  FP32
- * arithmetic.  Device scratch of 4 volumes, stream-ordered.  Synchronous with
+ * arithmetic.  Device scratch of 10 volumes (13 when q is on the host or NULL),
+ * stream-ordered: the dual pair alternates between two buffers.  Synchronous with
  * host buffers, else asynchronous on `stream`.
  */
 FBL_API fbl_status prox_tv(const int32_t dims[3], const float *v, double lambda, double x_max, int32_t iters,

@@ -801,22 +801,33 @@ extern "C" fbl_status prox_tv(const int32_t dims[3], const float *v, double lamb
     const void *vd = nullptr;
     fbl_status st;
     if ((st = device_input(v, n * sizeof(float), vs, &vd, s))) return st;
-    // q (3 volumes, unless the caller's device q is used), r (3), y (1)
+    // two dual pairs: (caller's device q or scratch, r0), (q1, r1); and y
     const bool q_dev = q && is_device_ptr(q);
-    CK(scratch.alloc((q_dev ? 4 : 7) * n * sizeof(float), s), "scratch");
-    float *r = (float *)scratch.p, *y = r + 3 * n;
-    float *qd = q_dev ? q : y + n;
-    if (q && !q_dev && q_in) CK(cudaMemcpyAsync(qd, q, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s), "q H2D");
+    CK(scratch.alloc((q_dev ? 10 : 13) * n * sizeof(float), s), "scratch");
+    float *base = (float *)scratch.p;
+    float *const qp[2] = {q_dev ? q : base + 10 * n, base + 3 * n};
+    float *const rp[2] = {base, base + 6 * n};
+    float *y = base + 9 * n;
+    const float *q_start = nullptr;
+    if (q_in) {
+        if (!q_dev) CK(cudaMemcpyAsync(qp[0], q, 3 * n * sizeof(float), cudaMemcpyHostToDevice, s), "q H2D");
+        q_start = qp[0];
+    }
     const bool x_dev = is_device_ptr(x);
     float *xd = x;
     if (!x_dev) {
         CK(xs.alloc(n * sizeof(float), s), "output staging");
         xd = (float *)xs.p;
     }
-    CK(launch_tv_prox((const float *)vd, nx, ny, nz, (float)lambda, (float)x_max, iters, q_in ? 1 : 0, qd, r, y,
-                      xd, s),
+    int cur = 1;  // the start goes to pair 1 (it reads pair 0's q)
+    CK(launch_tv_prox((const float *)vd, nx, ny, nz, (float)lambda, (float)x_max, iters, q_start, qp, rp, y, xd,
+                      &cur, s),
        "TV prox kernels");
-    if (q && !q_dev) CK(cudaMemcpyAsync(q, qd, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s), "q D2H");
+    if (q) {
+        if (q_dev && cur != 0)
+            CK(cudaMemcpyAsync(q, qp[cur], 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, s), "q copy");
+        if (!q_dev) CK(cudaMemcpyAsync(q, qp[cur], 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s), "q D2H");
+    }
     if (!x_dev) CK(cudaMemcpyAsync(x, xd, n * sizeof(float), cudaMemcpyDeviceToHost, s), "x D2H");
     if (!x_dev || (q && !q_dev) || !is_device_ptr(v)) CK(cudaStreamSynchronize(s), "prox_tv");
     return FBL_OK;
@@ -898,9 +909,10 @@ struct fbl_solver {
     PropState *h_ps = nullptr;                    // pinned mirror (host-loop mode)
     float *d_mlp = nullptr;                       // network parameters, NULL until set
     float margin = 0.25f;
-    // TV prox (reg = FBL_REG_TV): b, y, q[3], r[3] as consecutive FP32 volumes
+    // TV prox (reg = FBL_REG_TV): b, y, then (q[3], r[3]) twice, consecutive FP32 volumes
     float *tv_buf = nullptr;
-    bool tv_have_q = false;                       // q holds the previous prox's dual
+    int tv_cur = 0;                               // the pair holding the previous prox's dual
+    bool tv_have_q = false;
 };
 
 namespace {
@@ -914,11 +926,12 @@ cudaError_t solver_prox(fbl_solver *s, double alpha, int *npp, cudaStream_t st) 
         return launch_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu), (float)s->p.x_max,
                               s->tr, xdt, s->partials, npp, st);
     const size_t n = (size_t)s->L.nx * s->L.ny * s->L.nz;
-    float *b = s->tv_buf, *y = b + n, *q = y + n, *r = q + 3 * n;
+    float *b = s->tv_buf, *y = b + n;
+    float *const q[2] = {y + n, y + 7 * n}, *const r[2] = {y + 4 * n, y + 10 * n};
     const int warm = s->p.tv_warm && s->tv_have_q;
     cudaError_t e = launch_tv_prox_zi(s->st, s->L, s->grad, (float)alpha, (float)(alpha * s->p.mu),
-                                      (float)s->p.x_max, s->p.tv_iters, warm, b, q, r, y, s->tr, xdt, s->partials,
-                                      npp, st);
+                                      (float)s->p.x_max, s->p.tv_iters, warm, b, q, r, &s->tv_cur, y, s->tr, xdt,
+                                      s->partials, npp, st);
     if (e == cudaSuccess) s->tv_have_q = true;
     return e;
 }
@@ -1678,8 +1691,8 @@ extern "C" fbl_status fblisa_create(const fbl_geometry *g, const fbl_params *p, 
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, nvox * sizeof(float));
     if (e == cudaSuccess && p->reg == FBL_REG_TV) {
-        // b, y and the dual pair (q, r) of the TV prox: 8 volumes of FP32
-        e = cudaMalloc(&s->tv_buf, 8 * nvox * sizeof(float));
+        // b, y and two dual pairs (q, r) of the TV prox: 14 volumes of FP32
+        e = cudaMalloc(&s->tv_buf, 14 * nvox * sizeof(float));
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->xstage, nvox * es);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_views, (size_t)d.n_views * sizeof(int32_t));

@@ -173,20 +173,24 @@ cudaError_t launch_prox_zi(const void *vol, ZLayout L, const float *gzi, float a
 int prox_zi_num_partials(int nx, int ny, int nz);
 
 // Total variation (k_tv.cu).  Volumes in a memory order (n0 fastest, n1, n2),
-// dual fields as 3 such volumes.  tv_prox: x = prox of lam TV + indicator of
-// [0, xmax] at v by `iters` FGP iterations, from q (q_in) or zero; q ends as
-// the last dual; r and y are scratch (3 volumes, 1 volume).
+// dual fields as 3 such volumes; the dual pair (q, r) alternates between
+// (q[0], r[0]) and (q[1], r[1]), *cur naming the pair in use.  tv_prox:
+// x = prox of lam TV + indicator of [0, xmax] at v by `iters` FGP iterations
+// from q_start (NULL: zero), written to pair *cur first; *cur ends at the pair
+// holding the last dual; y is scratch (1 volume).
 bool tv_dims_ok(int n0, int n1, int n2);
-cudaError_t launch_tv_prox(const float *v, int n0, int n1, int n2, float lam, float xmax, int iters, int q_in,
-                           float *q, float *r, float *y, float *x, cudaStream_t st);
+cudaError_t launch_tv_prox(const float *v, int n0, int n1, int n2, float lam, float xmax, int iters,
+                           const float *q_start, float *const q[2], float *const r[2], float *y, float *x, int *cur,
+                           cudaStream_t st);
 int tv_norm_num_partials(int n0, int n1, int n2);
 cudaError_t launch_tv_norm(const float *x, int n0, int n1, int n2, double *partials, cudaStream_t st);
-// The solver's TV trial point: b = x - alpha g ([j][i][k]), FGP from q
-// (warm) or zero, then x_bar = P_C(b - lam K^T q) into trial with the three
-// partial sums of launch_prox_zi (same block count).
+// The solver's TV trial point: b = x - alpha g ([j][i][k]), FGP from the
+// dual in pair *cur (warm) or zero, started in the other pair, then
+// x_bar = P_C(b - lam K^T q) into trial with the three partial sums of
+// launch_prox_zi (same block count); *cur ends at the last dual's pair.
 cudaError_t launch_tv_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float lam, float xmax,
-                              int iters, int warm, float *b, float *q, float *r, float *y, void *trial, int dtype,
-                              double *partials, int *n_partials, cudaStream_t st);
+                              int iters, int warm, float *b, float *const q[2], float *const r[2], int *cur,
+                              float *y, void *trial, int dtype, double *partials, int *n_partials, cudaStream_t st);
 
 // Flat prox on n elements (public prox_reduce).
 cudaError_t launch_prox_flat(const void *x, const float *gr, int64_t n, float alpha, float amu,

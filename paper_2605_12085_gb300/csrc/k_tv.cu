@@ -12,8 +12,11 @@
 //     q' = P_ball(r + K y / (12 lambda)),  r = q' + theta (q' - q),  q = q'  (k_tv_dual)
 //
 // and the result P_C(b - lambda K^T q).  Both kernels stream the volumes once
-// (memory-bound: 20 and 52 bytes per voxel); k_tv_dual reads no neighbour of
-// q or r, so it updates them in place.  Volumes are in any memory order given
+// (memory-bound: 20 and 52 bytes per voxel).  The dual pair (q, r) alternates
+// between two buffers: k_tv_dual reads one pair and writes the other.  (Updated
+// in place -- every thread storing to the six lines it had just loaded -- the
+// same kernel ran 8x slower, its loads waiting ~20 us with DRAM 8% busy.)
+// Volumes are in any memory order given
 // by (n0 fastest, n1, n2); a dual field is 3 volumes, component c along axis c
 // of that order (the isotropic norm does not depend on the order).  The
 // solver's volumes are in gradient order [j][i][k] (n0 = nz, n1 = nx, n2 = ny);
@@ -60,7 +63,9 @@ __global__ void __launch_bounds__(TV_NT) k_tv_primal(const float *__restrict__ b
 }
 
 __global__ void __launch_bounds__(TV_NT) k_tv_dual(const float *__restrict__ y, Dims d, float inv12lam,
-                                                   float theta, float *__restrict__ q, float *__restrict__ r) {
+                                                   float theta, const float *__restrict__ q,
+                                                   const float *__restrict__ r, float *__restrict__ qo,
+                                                   float *__restrict__ ro) {
     const int a0 = blockIdx.x * TV_NT + threadIdx.x, a1 = blockIdx.y, a2 = blockIdx.z;
     if (a0 >= d.n0) return;
     const size_t N = d.N(), e = ((size_t)a2 * d.n1 + a1) * d.n0 + a0;
@@ -78,26 +83,27 @@ __global__ void __launch_bounds__(TV_NT) k_tv_dual(const float *__restrict__ y, 
     g1 *= sc;
     g2 *= sc;
     const float o0 = q[e], o1 = q[N + e], o2 = q[2 * N + e];
-    q[e] = g0;
-    q[N + e] = g1;
-    q[2 * N + e] = g2;
-    r[e] = fmaf(theta, g0 - o0, g0);
-    r[N + e] = fmaf(theta, g1 - o1, g1);
-    r[2 * N + e] = fmaf(theta, g2 - o2, g2);
+    qo[e] = g0;
+    qo[N + e] = g1;
+    qo[2 * N + e] = g2;
+    ro[e] = fmaf(theta, g0 - o0, g0);
+    ro[N + e] = fmaf(theta, g1 - o1, g1);
+    ro[2 * N + e] = fmaf(theta, g2 - o2, g2);
 }
 
-// q's components without a difference set to zero, r = q (zero = 1: both zero).
-__global__ void __launch_bounds__(TV_NT) k_tv_start(Dims d, int zero, float *__restrict__ q,
-                                                    float *__restrict__ r) {
+// The starting pair (qo, ro) = (q, q) with q's components without a
+// difference set to zero (q = NULL: both zero).
+__global__ void __launch_bounds__(TV_NT) k_tv_start(Dims d, const float *__restrict__ q, float *__restrict__ qo,
+                                                    float *__restrict__ ro) {
     const int a0 = blockIdx.x * TV_NT + threadIdx.x, a1 = blockIdx.y, a2 = blockIdx.z;
     if (a0 >= d.n0) return;
     const size_t N = d.N(), e = ((size_t)a2 * d.n1 + a1) * d.n0 + a0;
     const bool h[3] = {a0 < d.n0 - 1, a1 < d.n1 - 1, a2 < d.n2 - 1};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float v = (zero || !h[c]) ? 0.f : q[c * N + e];
-        q[c * N + e] = v;
-        r[c * N + e] = v;
+        const float v = (!q || !h[c]) ? 0.f : q[c * N + e];
+        qo[c * N + e] = v;
+        ro[c * N + e] = v;
     }
 }
 
@@ -178,19 +184,23 @@ __global__ void __launch_bounds__(TV_TX *TV_TY) k_tv_final_zi(const T *__restric
 
 dim3 tv_grid(const Dims &d) { return dim3((d.n0 + TV_NT - 1) / TV_NT, d.n1, d.n2); }
 
-// FGP iterations on (q, r) from the start already in r: theta_k from
+// FGP iterations from the pair (q[*cur], r[*cur]), alternating between the
+// two pairs; *cur ends at the pair holding the last dual.  theta_k from
 // t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2.
-cudaError_t fgp_iterations(const float *b, const Dims &d, float lam, float xmax, int iters, float *y, float *q,
-                           float *r, cudaStream_t st) {
+cudaError_t fgp_iterations(const float *b, const Dims &d, float lam, float xmax, int iters, float *y,
+                           float *const q[2], float *const r[2], int *cur, cudaStream_t st) {
     const dim3 grid = tv_grid(d);
     const float inv12 = (float)(1.0 / (12.0 * (double)lam));
     double t = 1.0;
+    int c = *cur;
     for (int it = 0; it < iters; ++it) {
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        k_tv_primal<<<grid, TV_NT, 0, st>>>(b, r, d, lam, xmax, y);
-        k_tv_dual<<<grid, TV_NT, 0, st>>>(y, d, inv12, (float)((t - 1.0) / tn), q, r);
+        k_tv_primal<<<grid, TV_NT, 0, st>>>(b, r[c], d, lam, xmax, y);
+        k_tv_dual<<<grid, TV_NT, 0, st>>>(y, d, inv12, (float)((t - 1.0) / tn), q[c], r[c], q[1 - c], r[1 - c]);
+        c = 1 - c;
         t = tn;
     }
+    *cur = c;
     return cudaGetLastError();
 }
 
@@ -198,16 +208,17 @@ cudaError_t fgp_iterations(const float *b, const Dims &d, float lam, float xmax,
 
 bool tv_dims_ok(int n0, int n1, int n2) { return n0 > 0 && n1 > 0 && n2 > 0 && n1 <= 65535 && n2 <= 65535; }
 
-cudaError_t launch_tv_prox(const float *v, int n0, int n1, int n2, float lam, float xmax, int iters, int q_in,
-                           float *q, float *r, float *y, float *x, cudaStream_t st) {
+cudaError_t launch_tv_prox(const float *v, int n0, int n1, int n2, float lam, float xmax, int iters,
+                           const float *q_start, float *const q[2], float *const r[2], float *y, float *x, int *cur,
+                           cudaStream_t st) {
     const Dims d{n0, n1, n2};
     const dim3 grid = tv_grid(d);
-    k_tv_start<<<grid, TV_NT, 0, st>>>(d, q_in ? 0 : 1, q, r);
+    k_tv_start<<<grid, TV_NT, 0, st>>>(d, q_start, q[*cur], r[*cur]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (lam > 0.f && (e = fgp_iterations(v, d, lam, xmax, iters, y, q, r, st)) != cudaSuccess) return e;
+    if (lam > 0.f && (e = fgp_iterations(v, d, lam, xmax, iters, y, q, r, cur, st)) != cudaSuccess) return e;
     // result P_C(v - lam K^T q): the primal kernel on q (lam = 0 gives P_C(v))
-    k_tv_primal<<<grid, TV_NT, 0, st>>>(v, q, d, lam > 0.f ? lam : 0.f, xmax, x);
+    k_tv_primal<<<grid, TV_NT, 0, st>>>(v, q[*cur], d, lam > 0.f ? lam : 0.f, xmax, x);
     return cudaGetLastError();
 }
 
@@ -220,8 +231,8 @@ cudaError_t launch_tv_norm(const float *x, int n0, int n1, int n2, double *parti
 }
 
 cudaError_t launch_tv_prox_zi(const void *vol, ZLayout L, const float *gzi, float alpha, float lam, float xmax,
-                              int iters, int warm, float *b, float *q, float *r, float *y, void *trial, int dtype,
-                              double *partials, int *n_partials, cudaStream_t st) {
+                              int iters, int warm, float *b, float *const q[2], float *const r[2], int *cur,
+                              float *y, void *trial, int dtype, double *partials, int *n_partials, cudaStream_t st) {
     const int nb = (L.nx * L.ny + TV_TY - 1) / TV_TY;
     if (nb != prox_zi_num_partials(L.nx, L.ny, L.nz)) return cudaErrorInvalidConfiguration;
     const dim3 blk(TV_TX, TV_TY);
@@ -231,22 +242,26 @@ cudaError_t launch_tv_prox_zi(const void *vol, ZLayout L, const float *gzi, floa
         case FBL_F16: k_tv_rhs_zi<<<nb, blk, 0, st>>>((const __half *)vol, L, gzi, alpha, b); break;
         default: k_tv_rhs_zi<<<nb, blk, 0, st>>>((const float *)vol, L, gzi, alpha, b); break;
     }
-    k_tv_start<<<tv_grid(d), TV_NT, 0, st>>>(d, warm ? 0 : 1, q, r);
+    // the start goes to the other pair (from the last dual when warm)
+    const int c0 = *cur;
+    k_tv_start<<<tv_grid(d), TV_NT, 0, st>>>(d, warm ? q[c0] : nullptr, q[1 - c0], r[1 - c0]);
+    *cur = 1 - c0;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (lam > 0.f && (e = fgp_iterations(b, d, lam, xmax, iters, y, q, r, st)) != cudaSuccess) return e;
+    if (lam > 0.f && (e = fgp_iterations(b, d, lam, xmax, iters, y, q, r, cur, st)) != cudaSuccess) return e;
     const float lm = lam > 0.f ? lam : 0.f;
+    const float *qf = q[*cur];
     switch (dtype) {
         case FBL_BF16:
-            k_tv_final_zi<<<nb, blk, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, b, q, lm, xmax,
+            k_tv_final_zi<<<nb, blk, 0, st>>>((const __nv_bfloat16 *)vol, L, gzi, b, qf, lm, xmax,
                                               (__nv_bfloat16 *)trial, partials);
             break;
         case FBL_F16:
-            k_tv_final_zi<<<nb, blk, 0, st>>>((const __half *)vol, L, gzi, b, q, lm, xmax, (__half *)trial,
+            k_tv_final_zi<<<nb, blk, 0, st>>>((const __half *)vol, L, gzi, b, qf, lm, xmax, (__half *)trial,
                                               partials);
             break;
         default:
-            k_tv_final_zi<<<nb, blk, 0, st>>>((const float *)vol, L, gzi, b, q, lm, xmax, (float *)trial,
+            k_tv_final_zi<<<nb, blk, 0, st>>>((const float *)vol, L, gzi, b, qf, lm, xmax, (float *)trial,
                                               partials);
             break;
     }
