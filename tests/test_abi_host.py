@@ -79,3 +79,28 @@ def test_host_helpers_reject_bad_arguments(fbl):
         fbl.fbl_schedule(10, 4, 10, 1.0, 1.5, 3)
     with pytest.raises(fbl.FblError):
         fbl.fbl_epoch_batches(1, 1, 10, 11)
+
+
+def test_params_defaults_read_back(fbl):
+    # the fields after fixed_step (reg, tv_iters, tv_warm, x_max) land where the C struct has them
+    import math
+    p = fbl.params_default()
+    assert (p.alpha0, p.beta, p.mu, p.N0, p.max_backtracks) == (1e-3, 0.5, 1.0, 8, 60)
+    assert (p.fixed_step, p.reg, p.tv_iters, p.tv_warm) == (0, fbl.REG_L1, 20, 1)
+    assert math.isinf(p.x_max) and p.x_max > 0
+
+
+def test_tv_calls_reject_bad_arguments(fbl):
+    import numpy as np
+    with pytest.raises(fbl.FblError) as e:
+        fbl.prox_tv(np.zeros((0, 2, 2), np.float32), 0.1, 5)
+    assert e.value.status == 1
+    with pytest.raises(fbl.FblError) as e:
+        fbl.prox_tv(np.zeros((2, 2, 2), np.float32), -0.1, 5)
+    assert e.value.status == 1
+    with pytest.raises(fbl.FblError) as e:
+        fbl.prox_tv(np.zeros((2, 2, 2), np.float32), 0.1, 5, x_max=0.0)
+    assert e.value.status == 1
+    with pytest.raises(fbl.FblError) as e:
+        fbl.tv_norm(np.zeros((2, 0, 2), np.float32))
+    assert e.value.status == 1
