@@ -70,6 +70,8 @@ def parse():
                     help="also run the paper-shaped 560^3 cases with RE / PSNR over time (several minutes)")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
+    ap.add_argument("--tv-only", type=int, default=0,
+                    help="time only prox_tv (20 FGP iterations) on the phantom of --workload (--steps calls)")
     ap.add_argument("--fdk-only", type=int, default=0,
                     help="time only FDK over all views of --workload (--steps reconstructions after one warm-up)")
     return ap.parse_args()
@@ -759,6 +761,38 @@ def run_fdk_only(args):
     return {"workload": args.workload, "fdk": rec}
 
 
+def run_tv_only(args):
+    """prox_tv alone on the workload's phantom (one GPU): a side measurement,
+    not the contract line."""
+    import torch
+    import paper_2605_12085_gb300 as fbl
+    import synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS[args.workload]
+    g = wl.geom
+    xt = synth.phantom(g, wl.n_ellipsoids, wl.seed_phantom, inclusions=wl.inclusions, texture_std=wl.texture_std)
+    v = torch.from_numpy(xt).to(device)
+    q = torch.zeros((3,) + tuple(v.shape), dtype=torch.float32, device=device)
+    x = torch.empty_like(v)
+    fgp = 20
+    fbl.prox_tv(v, 0.01, fgp, q=q, x=x)
+    torch.cuda.synchronize(device)
+    stream = torch.cuda.current_stream(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps)
+    e0.record(stream)
+    for _ in range(reps):
+        fbl.prox_tv(v, 0.01, fgp, q=q, x=x)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / reps
+    byt = float(g.n_vox) * (24 + 72 * fgp + 20)
+    return {"workload": args.workload, "prox_tv": {"voxels": g.n_vox, "fgp_iterations": fgp, "ms": ms,
+                                                  "achieved_gbs": byt / (ms * 1e-3) / 1e9}}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -1000,6 +1034,10 @@ def main():
     if args.fdk_only:
         if rank == 0:
             print(json.dumps(run_fdk_only(args)), flush=True)
+        return 0
+    if args.tv_only:
+        if rank == 0:
+            print(json.dumps(run_tv_only(args)), flush=True)
         return 0
     if world > 1:
         import torch.distributed as dist
