@@ -262,7 +262,8 @@ FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, i
  *   out3_host[1] = 1/2 ||A x - b||^2,
  *   out3_host[2] = RE = ||x - x_true|| / ||x_true||   (0 when x_true is NULL).
  * x, x_true: [nz][ny][nx] of x_dtype; b: the full sinogram of b_dtype.  FP32
- * projection, FP64 sums.  Returns after the values are on the host.
+ * projection, FP64 sums.  Returns after the values are on the host.  With
+ * R = mu TV (FBL_REG_TV) the objective is out3_host[1] + mu * tv_norm(x).
  */
 FBL_API fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtype, const void *b,
                             int32_t b_dtype, double mu, const void *x_true, double *out3_host,
