@@ -278,15 +278,26 @@ cudaError_t launch_fdk_filter(const void *y, int y_dtype, int n_sel, int nu, int
     return cudaGetLastError();
 }
 
+// One launch per FDK_SUB views (accumulating into the volume): every block of a
+// launch reads the same few views, whose filtered rows then stay in L2 for
+// the blocks of neighbouring voxel rows (a launch over all views of a chunk
+// let blocks drift apart by up to the whole chunk and re-read from DRAM).
+constexpr int FDK_SUB = 32;
+
 cudaError_t launch_fdk_bp(const float *qt, const double *view_csw, int n_sel, int nx, int ny, int nz, int nu,
                           int nv, double vx, double vy, double vz, double sod, double sdd, double du, double dv,
                           int accumulate, float *gzi, cudaStream_t st) {
     const double m = sod / sdd;
     dim3 block(32, FDK_WARPS);
     dim3 grid((nx + FDK_WARPS - 1) / FDK_WARPS, ny, (nz + 32 * FDK_KPL - 1) / (32 * FDK_KPL));
-    k_fdk_bp<<<grid, block, 0, st>>>((const float2 *)qt, (const FdkView *)view_csw, n_sel, nx, ny, nz, nu, nv, vx,
-                                     vy, vz, sod, 1.0 / (du * m), 1.0 / (dv * m), 0.5 * (nu - 1), 0.5 * (nv - 1),
-                                     accumulate, gzi);
+    const size_t vstride = (size_t)(nu + 1) * fdk_row_stride(nv);  // float2 entries per view
+    for (int s0 = 0; s0 < n_sel; s0 += FDK_SUB) {
+        const int ns = n_sel - s0 < FDK_SUB ? n_sel - s0 : FDK_SUB;
+        k_fdk_bp<<<grid, block, 0, st>>>((const float2 *)qt + (size_t)s0 * vstride,
+                                         (const FdkView *)view_csw + s0, ns, nx, ny, nz, nu, nv, vx, vy, vz, sod,
+                                         1.0 / (du * m), 1.0 / (dv * m), 0.5 * (nu - 1), 0.5 * (nv - 1),
+                                         (accumulate || s0 > 0) ? 1 : 0, gzi);
+    }
     return cudaGetLastError();
 }
 
