@@ -18,7 +18,7 @@
 // backprojection reads the four taps of a voxel as two aligned float2 loads of
 // consecutive entries along z and needs no bounds test at the edges.  The
 // block restages its results in shared memory and stores them as float4s.
-// k_fdk_bp (= or += over chunks of views): a warp owns one (i, j) voxel
+// k_fdk_bp (launched per 32 views, = for the first launch, += after): a warp owns one (i, j) voxel
 // column and 32 * FDK_KPL voxels along z (lane l: k0 + l + 32 t).  The FP64
 // geometry of a (column, view) pair (detector column and weight, the
 // vertical map k -> v) is formed by one thread -- lane l of the warp takes
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(FDK_FT) k_fdk_filter(const TY *__restrict__ y,
                                                        double cv, float *__restrict__ qt) {
     extern __shared__ float fsm[];
     const int lp = nu + 2 * FR_PAD, rl = fr_row_len(nu), KH = fr_kh(nu);
-    float *P = fsm;                      // [FDK_ROWS][rl] weighted rows, padded and skewed
+    float *P = fsm;                      // [FDK_ROWS][rl] weighted rows, zero-padded
     float *Q = fsm + FDK_ROWS * rl;      // [FDK_ROWS][nu] filtered rows
     float *H = Q + FDK_ROWS * nu;        // t h(k t) for odd k in [-KH, KH], at (k + KH) / 2
     const int s = blockIdx.y, r0 = blockIdx.x * FDK_ROWS;
