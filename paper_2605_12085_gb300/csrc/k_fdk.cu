@@ -18,7 +18,8 @@
 // backprojection reads the four taps of a voxel as two aligned float2 loads of
 // consecutive entries along z and needs no bounds test at the edges.  The
 // block restages its results in shared memory and stores them as float4s.
-// k_fdk_bp (launched per 32 views, = for the first launch, += after): a warp owns one (i, j) voxel
+// k_fdk_bp (one launch per 32 views; each adds into the volume but the very
+// first, which writes it): a warp owns one (i, j) voxel
 // column and 32 * FDK_KPL voxels along z (lane l: k0 + l + 32 t).  The FP64
 // geometry of a (column, view) pair (detector column and weight, the
 // vertical map k -> v) is formed by one thread -- lane l of the warp takes
