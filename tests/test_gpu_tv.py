@@ -118,6 +118,31 @@ def test_solver_tv_matches_oracle():
     assert fbl.tv_norm(x) < fbl.tv_norm(x1)
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_solver_tv_low_precision_storage(dtype):
+    # the storage types of the iterate (FP32 arithmetic): the same steps as the
+    # FP32 TV solver and iterates within the storage rounding
+    import torch
+    import paper_2605_12085_gb300 as fbl
+    wl, xt, b32 = _wl()
+    g = wl.geom
+    code, td = {"bf16": (fbl.BF16, torch.bfloat16), "f16": (fbl.F16, torch.float16)}[dtype]
+    kw = dict(alpha0=1e-3, beta=0.5, mu=20.0, N0=wl.N0, seed=wl.seed_batches, reg=fbl.REG_TV, tv_iters=10,
+              x_max=0.8)
+    G = fbl.geometry_create(g)
+    n_it = 4
+    S32 = fbl.fblisa_create(G, fbl.params_default(**kw))
+    x32 = cuda(np.zeros(g.vol_shape, np.float32))
+    tr32 = [S32.step(x32, cuda(b32)) for _ in range(n_it)]
+    S = fbl.fblisa_create(G, fbl.params_default(x_dtype=code, b_dtype=code, **kw))
+    x = cuda(np.zeros(g.vol_shape, np.float32), td)
+    tr = [S.step(x, cuda(b32, td)) for _ in range(n_it)]
+    assert [t["alpha"] for t in tr] == [t["alpha"] for t in tr32]
+    xh = host(x)
+    assert np.isfinite(xh).all() and xh.min() >= 0.0 and xh.max() <= 0.8
+    assert rel_l2(xh, host(x32)) <= 1e-2
+
+
 def test_solver_l1_box_host_graph_and_oracle():
     import paper_2605_12085_gb300 as fbl
     wl, xt, b32 = _wl()
