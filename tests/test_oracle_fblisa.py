@@ -99,6 +99,51 @@ def test_minibatch_objective_is_unbiased():
         assert np.mean(vals) == pytest.approx(full, rel=1e-12)
 
 
+def test_fb_step_quantities_are_unbiased_and_consistent():
+    # eq. (2.5) through fb_step itself: over all C(6, 2) mini-batches the mean
+    # of f_N(x) is 1/2 ||A x - b||^2 and the mean stochastic gradient is
+    # A^T (A x - b) from the explicit matrix.  The gradient is read off
+    # x_bar = x - alpha g (mu = 0 and x large, so nothing is clipped); each
+    # trial's f_N(x_bar) equals f_N at x_bar from a second step.
+    g, xt, b = _problem(8, _geom(views=6))
+    A = _dense_A(g, range(g.n_views))
+    x = 5.0 + np.random.default_rng(8).uniform(0, 1, g.vol_shape)
+    r_all = A @ x.ravel() - b.ravel()
+    alpha = 1e-4
+    p = fblisa.Params(alpha0=alpha, beta=0.5, mu=0.0)
+    fs, gs = [], []
+    for S in itertools.combinations(range(g.n_views), 2):
+        xb, rec = fblisa.fb_step(g, x, b, list(S), p, replay_alpha=alpha)
+        assert (xb > 0).all()
+        fs.append(rec.f_x)
+        gs.append(((x - xb) / alpha).ravel())
+        _, rec2 = fblisa.fb_step(g, xb, b, list(S), p, replay_alpha=alpha)
+        assert rec.trials[-1].f_xbar == pytest.approx(rec2.f_x, rel=1e-12)
+    assert np.mean(fs) == pytest.approx(0.5 * float(r_all @ r_all), rel=1e-12)
+    full_g = A.T @ r_all
+    assert np.abs(np.mean(gs, axis=0) - full_g).max() <= 1e-6 * np.abs(full_g).max()
+
+
+def test_sufficient_decrease_test_has_its_half():
+    # (2.3) on a quadratic: f(x_bar) = f(x) + g^T d + 1/2 d^T H d, so with d
+    # along the top eigenvector of H = A^T A (eigenvalue L) the test holds iff
+    # alpha <= 1/L: 0.9/L passes and 1.5/L fails (||d||^2/alpha in place of
+    # ||d||^2/(2 alpha) would pass both).
+    g, xt, b0 = _problem(9, _geom(views=6))
+    views = list(range(g.n_views))  # full batch
+    A = _dense_A(g, views)
+    _, sv, Vt = np.linalg.svd(A, full_matrices=False)
+    L = sv[0] ** 2
+    v = Vt[0]
+    x = np.full(g.vol_shape, 10.0)
+    b = (A @ x.ravel() - A @ v).reshape(b0.shape)  # A x - b = A v: g = L v
+    p = fblisa.Params(alpha0=1.0, beta=0.5, mu=0.0)
+    for a, want in ((0.9 / L, True), (1.5 / L, False)):
+        xb, rec = fblisa.fb_step(g, x, b, views, p, replay_alpha=a)
+        assert (xb > 0).all()
+        assert bool(rec.trials[-1].accepted) == want
+
+
 def _lipschitz(g, views):
     A = _dense_A(g, views)
     return g.n_views / len(views) * np.linalg.norm(A, 2) ** 2
