@@ -71,7 +71,7 @@ def test_analytic_ellipsoid_chords_converge():
     L = 64.0
     angles = (0.3, 1.1, 2.5, 4.0)
     errs = []
-    for n in (16, 32, 64):
+    for n in (20, 40, 80):  # voxels of 3.2, 1.6, 0.8 mm: none of unit size
         v = L / n
         g = synth.Geometry(nx=n, ny=n, nz=n, vx=v, vy=v, vz=v, n_views=len(angles), sod=400.0,
                            sdd=600.0, nu=40, nv=36, du=3.0, dv=3.0, angles=angles)
@@ -95,8 +95,10 @@ def test_analytic_ellipsoid_chords_converge():
 
 
 def test_single_voxel_lands_on_perspective_projection():
-    g = synth.Geometry(nx=24, ny=24, nz=24, vx=1.0, vy=1.0, vz=1.0, n_views=3, sod=300.0,
-                       sdd=450.0, nu=61, nv=61, du=0.75, dv=0.75, angles=(0.2, 1.9, 3.7))
+    # anisotropic voxels; the shadow's centroid (its taps are hat functions
+    # centred on the voxel) is the perspective image of the voxel centre
+    g = synth.Geometry(nx=24, ny=24, nz=24, vx=0.8, vy=1.25, vz=1.1, n_views=3, sod=300.0,
+                       sdd=450.0, nu=81, nv=81, du=0.75, dv=0.75, angles=(0.2, 1.9, 3.7))
     i, j, k = 17, 6, 15
     x = np.zeros(g.vol_shape)
     x[k, j, i] = 1.0
@@ -104,6 +106,7 @@ def test_single_voxel_lands_on_perspective_projection():
     px = (i - 11.5) * g.vx
     py = (j - 11.5) * g.vy
     pz = (k - 11.5) * g.vz
+    uu, vv = np.meshgrid(np.arange(g.nu), np.arange(g.nv))
     for vi, th in enumerate(g.angles):
         xi = px * math.cos(th) + py * math.sin(th)
         eta = -px * math.sin(th) + py * math.cos(th)
@@ -112,6 +115,8 @@ def test_single_voxel_lands_on_perspective_projection():
         iv = pz * mag / g.dv + 0.5 * (g.nv - 1)
         ivm, ium = np.unravel_index(np.argmax(y[vi]), y[vi].shape)
         assert abs(ium - iu) <= 1.0 and abs(ivm - iv) <= 1.0
+        w = y[vi] / y[vi].sum()
+        assert abs((w * uu).sum() - iu) <= 0.1 and abs((w * vv).sum() - iv) <= 0.1
 
 
 def _tiny_geom():
