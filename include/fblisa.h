@@ -228,7 +228,9 @@ FBL_API fbl_status backproject(const fbl_geometry *g, const void *y, int32_t y_d
  * x: [nz][ny][nx] float32, overwritten (zero when n_sel == 0).  Host or device
  * buffers; the library allocates its scratch (filtered projections of up to
  * 256 views, one volume).  FP32 filtering and interpolation, detector
- * coordinates from FP64 per voxel column.
+ * coordinates from FP64 per voxel column.  The row filter keeps 8 detector
+ * rows in shared memory: detectors wider than 3370 columns fail with
+ * FBL_E_CUDA (the launch is refused).
  */
 FBL_API fbl_status fdk(const fbl_geometry *g, const void *y, int32_t y_dtype, const int32_t *views,
                        int32_t n_sel, float *x, void *stream);
