@@ -284,7 +284,7 @@ FBL_API fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_dtyp
  * t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, starting from q (q_in = 1,
  * a warm start; components without a difference are zeroed) or from zero;
  * x = x(q) of the last q.  lambda = 0 gives clip(v, 0, x_max).
- * dims = {nx, ny, nz}; v, x: [nz][ny][nx] float32, x must not alias v;
+ * dims = {nx, ny, nz}; v, x: [nz][ny][nx] float32, x must not alias v (nor q);
  * q: NULL, or 3 * nx*ny*nz float32 [3][nz][ny][nx] (components along x, y, z),
  * read when q_in = 1 and holding the last dual on return.  Host or device
  * pointers (host ones are staged).  Needs ny, nz <= 65535, lambda >= 0,

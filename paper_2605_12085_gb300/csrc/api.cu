@@ -795,6 +795,7 @@ extern "C" fbl_status prox_tv(const int32_t dims[3], const float *v, double lamb
     if (!(lambda >= 0) || !std::isfinite(lambda) || !(x_max > 0) || iters < 0 || iters > 100000)
         return fail(FBL_E_INVAL, "prox_tv: need lambda >= 0, x_max > 0, 0 <= iters <= 100000");
     if ((const void *)x == (const void *)v) return fail(FBL_E_INVAL, "prox_tv: x must not alias v");
+    if (q && ((const void *)q == (const void *)v || q == x)) return fail(FBL_E_INVAL, "prox_tv: q must not alias v or x");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny * nz;
     AsyncBuf vs, scratch, xs;

@@ -104,3 +104,7 @@ def test_tv_calls_reject_bad_arguments(fbl):
     with pytest.raises(fbl.FblError) as e:
         fbl.tv_norm(np.zeros((2, 0, 2), np.float32))
     assert e.value.status == 1
+    q = np.zeros((3, 2, 2, 2), np.float32)
+    with pytest.raises(fbl.FblError) as e:
+        fbl.prox_tv(np.zeros((2, 2, 2), np.float32), 0.1, 5, q=q, x=q[0])  # x aliases q
+    assert e.value.status == 1
