@@ -253,6 +253,7 @@ FBL_API fbl_status residual_norm(const fbl_geometry *g, const void *x, int32_t x
  *   out3_host[0] = g^T (x_bar - x), out3_host[1] = ||x_bar - x||^2,
  *   out3_host[2] = ||x_bar||_1.
  * x, x_bar: n elements of x_dtype (x_bar must not alias x); g: n float32.
+ * n = 0 writes three zeros and touches no buffer (which may then be NULL).
  */
 FBL_API fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *g, int64_t n, double alpha,
                        double mu, void *xbar, double *out3_host, void *stream);
@@ -311,13 +312,19 @@ FBL_API fbl_status tv_norm(const int32_t dims[3], const float *x, double *out_ho
  * an allocation call could block or synchronize the device.  (The paper has
  * no counterpart; this is a library-level variant.)
  * It allocates nothing: the per-block partial sums and the three results
- * live in one fixed device array of 1.5 MiB inside the library, which every
- * GPU that loads the library keeps until the process exits.
- *   - x, g and x_bar must be device memory (no host staging is possible
- *     without allocating); other arguments as for prox_reduce.
+ * live in one fixed device array of 57 KiB inside the library, which every
+ * GPU that loads the library keeps until the process exits.  It launches the
+ * same kernels on the same grid as prox_reduce, so x_bar and the three sums
+ * are identical to prox_reduce's.
+ *   - x, g and x_bar must be device memory of the current device (no host
+ *     staging is possible without allocating); otherwise FBL_E_INVAL.  Other
+ *     arguments as for prox_reduce (n = 0 included).
  *   - n <= 134217728 (2^27, a 512^3 volume); larger n returns FBL_E_INVAL.
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and caches it; make that first call before any
+ *     stream capture begins.  The cached address is not valid after a
+ *     cudaDeviceReset.
+ *   - The call is synchronous: it returns once the three sums are on the host.
  *   - All calls share the one array, and it keeps the last call's contents:
  *     calls whose work overlaps on the GPU (other streams, other threads)
  *     race with each other and must be serialised by the caller.

@@ -320,8 +320,32 @@ def evaluate(geom: Geometry, x, b, mu: float, x_true=None, stream=None):
     return out[0], out[1], out[2]
 
 
-def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):
+def _prox_args(x, g, xbar, need_cuda: bool):
+    """Checks shared by the prox calls: g float32 with x's element count, xbar
+    (when given) of x's dtype and size; with need_cuda, all three CUDA tensors
+    of one device.  The C side cannot check buffer sizes itself."""
     n = int(np.prod(tuple(x.shape)))
+    if need_cuda:
+        import torch
+        for name, a in (("x", x), ("g", g), ("xbar", xbar)):
+            if not (isinstance(a, torch.Tensor) and a.is_cuda):
+                raise TypeError("prox_reduce_static: %s must be a CUDA tensor" % name)
+        if not (x.device == g.device == xbar.device):
+            raise ValueError("prox_reduce_static: x, g and xbar must be on one device")
+    if _dtype_code(g) != F32:
+        raise TypeError("prox: g must be float32")
+    if int(np.prod(tuple(g.shape))) != n:
+        raise ValueError("prox: g must have x's %d elements" % n)
+    if xbar is not None:
+        if _dtype_code(xbar) != _dtype_code(x):
+            raise TypeError("prox: xbar must have x's dtype")
+        if int(np.prod(tuple(xbar.shape))) != n:
+            raise ValueError("prox: xbar must have x's %d elements" % n)
+    return n
+
+
+def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):
+    n = _prox_args(x, g, xbar, need_cuda=False)
     if xbar is None:
         xbar = _like(x, tuple(x.shape), _dtype_code(x))
     out = (ctypes.c_double * 3)()
@@ -332,8 +356,9 @@ def prox_reduce(x, g, alpha: float, mu: float, xbar=None, stream=None):
 
 def prox_reduce_static(x, g, alpha: float, mu: float, xbar, stream=None):
     """prox_reduce without any allocation: x, g and xbar must be CUDA tensors
-    (xbar caller-provided); n <= 2^27.  Calls that overlap on the GPU race."""
-    n = int(np.prod(tuple(x.shape)))
+    (xbar caller-provided) of the current device; n <= 2^27.  Calls that
+    overlap on the GPU race."""
+    n = _prox_args(x, g, xbar, need_cuda=True)
     out = (ctypes.c_double * 3)()
     _check(lib.prox_reduce_static(_ptr(x), _dtype_code(x), _ptr(g), n, float(alpha), float(mu),
                                   _ptr(xbar), out, _stream(x, g, xbar, stream=stream)))

@@ -754,9 +754,14 @@ extern "C" fbl_status evaluate(const fbl_geometry *g, const void *x, int32_t x_d
 extern "C" fbl_status prox_reduce(const void *x, int32_t x_dtype, const float *gr, int64_t n,
                                   double alpha, double mu, void *xbar, double *out3_host,
                                   void *stream) {
-    if (!x || !gr || !xbar || !out3_host) return fail(FBL_E_INVAL, "prox_reduce: null argument");
+    if (!out3_host) return fail(FBL_E_INVAL, "prox_reduce: null argument");
     if (!valid_dtype(x_dtype)) return fail(FBL_E_INVAL, "prox_reduce: bad dtype");
     if (n < 0) return fail(FBL_E_INVAL, "prox_reduce: negative size");
+    if (n == 0) {  // empty sums; the buffers (possibly NULL) are not touched
+        out3_host[0] = out3_host[1] = out3_host[2] = 0.0;
+        return FBL_OK;
+    }
+    if (!x || !gr || !xbar) return fail(FBL_E_INVAL, "prox_reduce: null argument");
     if (x == xbar) return fail(FBL_E_INVAL, "prox_reduce: x_bar must not alias x");
     if (!(alpha > 0) || !std::isfinite(alpha) || !std::isfinite(mu))
         return fail(FBL_E_INVAL, "prox_reduce: need alpha > 0 and finite mu");
