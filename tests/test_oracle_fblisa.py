@@ -17,10 +17,13 @@
   which the closed form puts at K = 207 (epoch 23 for n_theta = 72), and the
   batch grows from 8 to 13 without reaching full batch within ~250
   iterations, as Sec. 3 reports for Case 3 (Fig. 2 discussion);
-* the per-epoch permutations are permutations with uniform marginals.
+* the per-epoch permutations are permutations with uniform marginals;
+* SplitMix64's first outputs equal the published reference outputs for three
+  starting states (tests/golden/splitmix64.txt).
 """
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -289,6 +292,17 @@ def test_batches_cover_epoch_and_pad_from_front():
         r = n_theta % N_t
         if r:
             assert batches[-1] == perm[-r:] + perm[:N_t - r]
+
+
+def test_splitmix64_matches_published_reference_outputs():
+    # The mini-batch generator is SplitMix64 from its publication: its first
+    # outputs from three starting states equal the published reference ones
+    # (tests/golden/splitmix64.txt), so a wrong constant, shift or increment fails.
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64.txt")
+    rows = [[int(t) for t in ln.split()] for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for state, *outs in rows:
+        assert [fblisa.splitmix64_draw(state, i) for i in range(len(outs))] == outs
 
 
 def test_splitmix64_stream_properties():

@@ -41,6 +41,10 @@ MUTATIONS = {
     "fb_residual_sign": ("fblisa.py", "    r = project(geom, x, views) - bS", "    r = bS - project(geom, x, views)", FB),
     "fb_epoch_key": ("fblisa.py", "    state = (seed ^ ((epoch * EPOCH_KEY) & MASK64)) & MASK64",
                      "    state = (seed ^ epoch) & MASK64", FB),
+    "fb_splitmix_constant": ("fblisa.py", "    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64",
+                             "    z = ((z ^ (z >> 27)) * 0x94D049BB133111EA) & MASK64", FB),
+    "fb_splitmix_shift": ("fblisa.py", "    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64",
+                          "    z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9) & MASK64", FB),
     # projector (oracle/joseph.c)
     "proj_no_obliquity": ("joseph.c", "    return V[a] * len / fabs(d[a]);", "    return V[a];", PROJ),
     "proj_no_voxel_size": ("joseph.c", "    return V[a] * len / fabs(d[a]);", "    return len / fabs(d[a]);", PROJ),
