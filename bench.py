@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the FB-LISA hot path on GB300: prints ONE JSON line.
 
-A step is one FB-LISA iteration (Algorithm 1, Steps 2a-2d): mini-batch
-selection, the residual projection and f_N(x), the gradient backprojection,
-and the backtracking loop of prox + trial-objective projections until (2.3)
-holds.  Default workload: 512^3 volume, 720 views, 768x768 detector,
-40-view mini-batches, FP32 storage (synthetic ellipsoid phantom with
-texture; data = A x_true + 1% Gaussian noise).
+The contract line's step is the metric's own quantity, "GUPS fwd+back at
+512^3 / 720 views": one forward projection A x of all 720 views (K1, 768x768
+detector, N samples per ray) and one backprojection A^T y of all 720 views
+(K2, N^3 voxel-views per view), both through the C ABI on buffers resident in
+HBM.  value = (720 nu nv N + 720 N^3) / step time.  Beside it:
 
-metric: GUPS = (ray-samples of every forward projection in the step +
-voxel-views of its backprojection) / step time.  A forward projection of
-N_t views counts N_t * nu * nv * N samples (N planes per ray); the
-backprojection counts N_t * N^3 voxel-views.
+  fblisa_iteration   one FB-LISA iteration (Algorithm 1, Steps 2a-2d: the
+                     mini-batch, the residual projection and f_N(x), the
+                     gradient backprojection, the backtracking loop of prox +
+                     trial objective until (2.3) holds) on 40-view
+                     mini-batches, with the rooflines of K1, K2 and K3;
+  time_to_objective  the metric's second part: wall time to the plain FP32
+                     method's objective within 1e-3, for learned proposal +
+                     BF16 + graph and for each of the three alone;
+  c2                 the 256^3 Poisson configuration run for its 20 epochs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,26 +39,29 @@ if ROOT not in sys.path:
 
 METRIC = "GUPS fwd+back at 512^3/720 views; FB-LISA time-to-1e-3 rel-err vs plain FP32"
 UNIT = "GUPS"
-# FP32 ops of one Joseph sample: 2 coordinate updates, 2 floors, 2 fractions,
-# 3 linear interpolations of 2 ops each, 1 accumulate
-OPS_PER_SAMPLE = 14
+# Algorithmic FP32 operations.  A Joseph sample of K1 (one ray, one plane):
+# 3 linear interpolations of 2 operations, 1 accumulation and the 2
+# coordinate steps along the ray, plus the 2 fractions of the crossing (10).
+# Each in-volume sample is 4 nonzeros of A; K2 spends, per nonzero, the tap
+# weight 1 - |d|, its product with the in-plane weight, the accumulation
+# and the step to the next row (4), so 16 per in-volume sample.
+K1_OPS_PER_SAMPLE = 10
+K2_OPS_PER_SAMPLE = 16
 K3_BYTES_PER_VOXEL = 12  # read x and g, write x_bar (FP32)
-# DRAM bytes (read + write) of one trial-objective projection launch of the
-# 512^3 / 768^2 / 40-view FP32 workload, from one ncu capture
-# (profiles/dram_traffic_c3_512.md); valid only for the projector source it
-# was taken on, so it is reported only while k_project.cu has that hash.
-K1_TRAFFIC = {"workload": "c3_512", "bytes_per_launch": 10.70e9,
-              "source_sha256": "136c4c66277e84cffa4159b3c72c89d6817f04f0fc72c59e5eb7476cdee14685"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c3_512")
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--iter-steps", type=int, default=10, help="timed FB-LISA iterations (fblisa_iteration)")
+    ap.add_argument("--c2", type=int, default=1, help="also run the 256^3 Poisson configuration (20 epochs)")
+    ap.add_argument("--tto-decompose", type=int, default=1,
+                    help="time-to-objective also for the learned proposal, BF16 and graph alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", type=int, default=1, help="also time BF16/FP16 storage")
     ap.add_argument("--variant-steps", type=int, default=5)
@@ -72,6 +79,8 @@ def parse():
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     ap.add_argument("--tv-only", type=int, default=0,
                     help="time only prox_tv (20 FGP iterations) on the phantom of --workload (--steps calls)")
+    ap.add_argument("--kernels-only", type=int, default=0,
+                    help="run only the hot kernels of one mini-batch of --workload (profiler captures)")
     ap.add_argument("--fdk-only", type=int, default=0,
                     help="time only FDK over all views of --workload (--steps reconstructions after one warm-up)")
     return ap.parse_args()
@@ -80,53 +89,6 @@ def parse():
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
-
-
-def k1_traffic(workload):
-    """The captured K1 DRAM traffic per launch, or None when it does not apply
-    (another workload, or the projector source changed since the capture)."""
-    import hashlib
-    if workload != K1_TRAFFIC["workload"]:
-        return None
-    src = os.path.join(ROOT, "paper_2605_12085_gb300", "csrc", "k_project.cu")
-    try:
-        with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
-    except OSError:
-        return None
-    return K1_TRAFFIC["bytes_per_launch"] if digest == K1_TRAFFIC["source_sha256"] else None
-
-
-def full_sweep(fbl, G, g, xd, device, reps=2):
-    """GUPS of the plain operators over every view: A x for all n_theta views
-    (N samples per ray) and A^T y for all views (N^3 voxel-views per view),
-    each timed with CUDA events after one warm-up, inputs resident in HBM."""
-    import torch
-    stream = torch.cuda.current_stream(device)
-    views = list(range(g.n_views))
-    y = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
-    gr = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    out = {}
-    for name, call in (("forward", lambda: fbl.project(G, xd, views, y=y)),
-                       ("back", lambda: fbl.backproject(G, y, views, x=gr))):
-        call()
-        torch.cuda.synchronize(device)
-        e0.record(stream)
-        for _ in range(reps):
-            call()
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        out[name + "_ms"] = e0.elapsed_time(e1) / reps
-    fwd_units = float(g.n_views) * g.nu * g.nv * g.nx
-    bp_units = float(g.n_views) * g.n_vox
-    del y, gr
-    return {"views": g.n_views, "forward_ms": out["forward_ms"], "back_ms": out["back_ms"],
-            "gups_forward": fwd_units / (out["forward_ms"] * 1e-3) / 1e9,
-            "gups_back": bp_units / (out["back_ms"] * 1e-3) / 1e9,
-            "gups_fwd_back": (fwd_units + bp_units) / ((out["forward_ms"] + out["back_ms"]) * 1e-3) / 1e9,
-            "units": "forward: n_views*nu*nv*N ray samples; back: n_views*N^3 voxel-views"}
 
 
 def batched_record(fbl, device, wls, label, proposal=False, steps=5, warmup=3):
@@ -624,9 +586,16 @@ def step_units(st, g):
 
 def active_samples(g, views):
     """Ray-plane samples K1 actually takes for these views (planes where the
-    crossing lies inside (-1, Nb) x (-1, nz)), from the geometry in float64."""
+    crossing lies inside (-1, Nb) x (-1, nz)), from the geometry in float64.
+    For every view of a square volume on a uniform orbit whose view count is a
+    multiple of 4, the counts of views a quarter turn apart are equal (the
+    setup maps onto itself), so the first quarter is counted four times."""
     import math
     import numpy as np
+    views = list(views)
+    if (g.angles is None and g.nx == g.ny and g.vx == g.vy and g.n_views % 4 == 0
+            and views == list(range(g.n_views))):
+        return 4 * active_samples(g, range(g.n_views // 4))
     cu, cv = 0.5 * (g.nu - 1), 0.5 * (g.nv - 1)
     V = (g.vx, g.vy, g.vz)
     Nn = (g.nx, g.ny, g.nz)
@@ -668,11 +637,12 @@ def active_samples(g, views):
     return total
 
 
-def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
+def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None, decompose=True):
     """Wall time (sum of CUDA-event step times; objective evaluations off the
-    clock) for plain FP32 FB-LISA and for learned proposal + BF16 storage +
-    graph capture to reach F(x) <= F* (1 + 1e-3), where F* is the plain
-    method's full objective after `epochs` epochs."""
+    clock) to reach F(x) <= F* (1 + 1e-3), where F* is the plain FP32 method's
+    full objective after `epochs` epochs: for learned proposal + BF16 storage
+    + graph capture and (decompose) for each of the three alone, on FP32
+    host-loop iterations otherwise."""
     import torch
     from paper_2605_12085_gb300 import proposal
     params, meta = proposal.load()
@@ -680,23 +650,21 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
     b16 = b.to(torch.bfloat16)
     xt_d = torch.from_numpy(xt).to(device) if xt is not None else None
 
-    def run(fast, max_epochs, target=None):
+    def run(learned, bf16, graph, max_epochs, target=None):
         p = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
-                               x_dtype=fbl.BF16 if fast else fbl.F32,
-                               b_dtype=fbl.BF16 if fast else fbl.F32,
-                               use_graph=1 if fast else 0, proposal=1 if fast else 0,
+                               x_dtype=fbl.BF16 if bf16 else fbl.F32,
+                               b_dtype=fbl.BF16 if bf16 else fbl.F32,
+                               use_graph=1 if graph else 0, proposal=1 if learned else 0,
                                autotune=1)
         S = fbl.fblisa_create(G, p)
-        if fast:
+        if learned:
             S.set_proposal(params, margin=0.25)
-        x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if fast else torch.float32,
-                        device=device)
-        bb = b16 if fast else b
+        x = torch.zeros(g.vol_shape, dtype=torch.bfloat16 if bf16 else torch.float32, device=device)
+        bb = b16 if bf16 else b
         elapsed, hist, k, trials = 0.0, [], 0, 0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        n_iter = sum(it for _, it in fbl.fbl_schedule(g.n_views, wl.N0, g.n_views, 1.0, 0.99,
-                                                        max_epochs))
+        n_iter = sum(it for _, it in fbl.fbl_schedule(g.n_views, wl.N0, g.n_views, 1.0, 0.99, max_epochs))
         while k < n_iter:
             e0.record(stream)
             st = S.step(x, bb)
@@ -707,30 +675,44 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None):
             trials += st["backtracks"] + 1
             if k % check_every == 0 or k == n_iter:
                 # BF16 -> FP32 widening is exact, so F is that of the stored iterate
-                F, _, re = fbl.evaluate(G, x.float() if fast else x, b, wl.mu, x_true=xt_d)
+                F, _, re = fbl.evaluate(G, x.float() if bf16 else x, b, wl.mu, x_true=xt_d)
                 hist.append((k, elapsed, F, re))
                 if target is not None and F <= target:
                     break
+        del S, x
         return hist, trials / max(k, 1)
 
-    plain, plain_trials = run(False, epochs)
+    plain, plain_trials = run(False, False, False, epochs)
     F_star = plain[-1][2]
     target = F_star * (1.0 + 1e-3)
     plain_hit = next(h for h in plain if h[2] <= target)
-    fast, fast_trials = run(True, 2 * epochs, target)
-    fast_hit = next((h for h in fast if h[2] <= target), None)
     out = {"F_star": F_star, "rel_tol": 1e-3, "epochs_for_F_star": epochs,
            "plain_fp32_s": plain_hit[1], "plain_iterations": plain_hit[0],
            "plain_rel_error_vs_x_true": plain_hit[3] if xt is not None else None,
-           "fast_rel_error_vs_x_true": (fast_hit[3] if fast_hit and xt is not None else None),
            "plain_trials_per_iteration": plain_trials,
-           "fast": "learned proposal + BF16 storage + graph-captured iteration",
-           "fast_s": fast_hit[1] if fast_hit else None,
-           "fast_iterations": fast_hit[0] if fast_hit else None,
-           "fast_trials_per_iteration": fast_trials,
-           "speedup": (plain_hit[1] / fast_hit[1]) if fast_hit else None,
            "check_every_iterations": check_every, "proposal_margin": 0.25,
            "proposal_traces": meta.get("traces")}
+    configs = [("fast", True, True, True)]
+    if decompose:
+        configs += [("learned_only", True, False, False), ("bf16_only", False, True, False),
+                    ("graph_only", False, False, True)]
+    for name, learned, bf16, graph in configs:
+        h, tr = run(learned, bf16, graph, 2 * epochs, target)
+        hit = next((r for r in h if r[2] <= target), None)
+        rec = {"learned_proposal": learned, "bf16_storage": bf16, "graph_captured": graph,
+               "s": hit[1] if hit else None, "iterations": hit[0] if hit else None,
+               "trials_per_iteration": tr, "rel_error_vs_x_true": hit[3] if hit and xt is not None else None,
+               "speedup": (plain_hit[1] / hit[1]) if hit else None}
+        if name == "fast":
+            out["fast"] = "learned proposal + BF16 storage + graph-captured iteration"
+            out["fast_s"] = rec["s"]
+            out["fast_iterations"] = rec["iterations"]
+            out["fast_trials_per_iteration"] = tr
+            out["fast_rel_error_vs_x_true"] = rec["rel_error_vs_x_true"]
+            out["speedup"] = rec["speedup"]
+        else:
+            out[name] = rec
+    del b16
     return out
 
 
@@ -793,6 +775,194 @@ def run_tv_only(args):
                                                   "achieved_gbs": byt / (ms * 1e-3) / 1e9}}
 
 
+def alu_peak_tops(clk, peaks):
+    """FP32 issue peak: 152 SMs x 128 lanes x the max SM clock seen (Tops/s)."""
+    sm_clock = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    return 152 * 128 * sm_clock * 1e6 / 1e12, sm_clock
+
+
+def alu_roofline(kernel, ops_per_sample, samples, avg_ms, algorithmic_bytes, clk, peaks, **extra):
+    peak, sm_clock = alu_peak_tops(clk, peaks)
+    achieved = ops_per_sample * samples / (avg_ms * 1e-3) / 1e12 if avg_ms else None
+    out = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": (achieved / peak) if achieved else None, "traffic": None,
+           "traffic_note": "null: DRAM bytes are not measured inside this run",
+           "algorithmic_bytes": algorithmic_bytes,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock seen)" % sm_clock,
+           "ops_per_sample": ops_per_sample, "in_volume_samples_per_launch": samples,
+           "avg_launch_ms": avg_ms}
+    out.update(extra)
+    return out
+
+
+def fblisa_iteration_record(fbl, G, g, wl, b, device, steps, warmup, peaks):
+    """One FB-LISA iteration (Steps 2a-2d, host loop, FP32) on the workload's
+    40-view mini-batches: GUPS over the work an iteration does (every forward
+    projection N_t nu nv N samples, the backprojection N_t N^3 voxel-views),
+    per-kernel CUDA-event times recorded by the library on the launching
+    stream, and the rooflines of the trial-objective projection (K1), the
+    gradient backprojection (K2) and the prox (K3)."""
+    import numpy as np
+    import torch
+    params = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
+                                max_backtracks=60)
+    S = fbl.fblisa_create(G, params)
+    x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(warmup):
+        S.step(x, b)
+    S.profile(True)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(device.index or 0)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    stats, batches = [], []
+    for _ in range(steps):
+        stats.append(S.step(x, b))
+        batches.append(S.last_batch())
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = S.profile(False)
+    units = sum(step_units(st, g) for st in stats)
+    samples = float(np.mean([active_samples(g, vs) for vs in batches[:3]]))
+    N_t = stats[0]["N_t"]
+    k1_ms, k1_n = prof["objective_projection"]
+    k2_ms, k2_n = prof["gradient_backprojection"]
+    k3_ms, k3_n = prof["prox_reduce"]
+    k3_avg = k3_ms / max(k3_n, 1)
+    k3_gbs = K3_BYTES_PER_VOXEL * g.n_vox / (k3_avg * 1e-3) / 1e9 if k3_n else None
+    return {
+        "what": "one FB-LISA iteration (Steps 2a-2d, host-loop line search), FP32 storage, "
+                "mini-batch %d views" % N_t,
+        "gups": units / (ms * 1e-3) / 1e9, "ms_per_iteration": ms / steps, "steps": steps, "warmup": warmup,
+        "backtracks_per_iteration": statistics.mean(st["backtracks"] for st in stats),
+        "in_volume_samples_per_projection": samples,
+        "roofline_k1": alu_roofline("k1_project, trial objective (Step 2c, eq. (2.3))", K1_OPS_PER_SAMPLE,
+                                    samples, k1_ms / max(k1_n, 1), g.n_vox * 4 + N_t * g.nu * g.nv * 4, clk,
+                                    peaks),
+        "roofline_k2": alu_roofline("k2_backproject, gradient (Step 2b, eq. (2.5))", K2_OPS_PER_SAMPLE,
+                                    samples, k2_ms / max(k2_n, 1),
+                                    N_t * g.nu * (g.nv + 16) * 4 + g.n_vox * 4, clk, peaks,
+                                    voxel_views_per_launch=float(N_t) * g.n_vox),
+        "roofline_k3": {"kernel": "k_prox_zi", "bound": "hbm", "achieved": k3_gbs,
+                        "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                        "frac": (k3_gbs / peaks["hbm_gbs"]) if k3_gbs else None,
+                        "bytes_per_voxel": K3_BYTES_PER_VOXEL, "avg_launch_ms": k3_avg},
+        "kernels": {name: {"ms": round(v[0], 3), "launches": v[1]} for name, v in prof.items()},
+        "clocks": clk,
+    }
+
+
+def sweep_units(g):
+    return float(g.n_views) * g.nu * g.nv * g.nx, float(g.n_views) * g.n_vox
+
+
+def c2_record(fbl, device, peaks):
+    """The 256^3 Poisson configuration as stated: 40-ellipsoid phantom with
+    small high-contrast inclusions, 360 views, 384x384 detector, log-Poisson
+    data (I_0 = 1e4), 20-view mini-batches growing by Step 1's schedule, 20
+    epochs, FP32; F, RE and backtracks at every epoch end (F and RE off the
+    clock), and the operators' full sweep at this size."""
+    import numpy as np
+    import torch
+    import synth
+    wl = synth.WORKLOADS["c2_256"]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    tune = fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    xt_d = torch.from_numpy(xt).to(device)
+    stream = torch.cuda.current_stream(device)
+    S = fbl.fblisa_create(G, fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0,
+                                                seed=wl.seed_batches))
+    x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    epochs, el, per_epoch = [], 0.0, {}
+    sched = fbl.fbl_schedule(g.n_views, wl.N0, g.n_views, 1.0, 0.99, wl.epochs)
+    for t, (N_t, iters) in enumerate(sched, start=1):
+        bts = []
+        for _ in range(iters):
+            e0.record(stream)
+            st = S.step(x, b)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            el += e0.elapsed_time(e1) * 1e-3
+            bts.append(st["backtracks"])
+            assert st["N_t"] == N_t
+        F, _, re = fbl.evaluate(G, x, b, wl.mu, x_true=xt_d)
+        epochs.append({"epoch": t, "N_t": N_t, "iterations": iters, "F": F, "rel_error": re,
+                       "backtracks_per_iteration": float(np.mean(bts)), "seconds": el})
+    fwd_u, bp_u = sweep_units(g)
+    y = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
+    gr = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
+    views = list(range(g.n_views))
+    fbl.project(G, x, views, y=y)
+    fbl.backproject(G, y, views, x=gr)
+    torch.cuda.synchronize(device)
+    t = {}
+    for name, call in (("forward", lambda: fbl.project(G, x, views, y=y)),
+                       ("back", lambda: fbl.backproject(G, y, views, x=gr))):
+        e0.record(stream)
+        for _ in range(3):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        t[name] = e0.elapsed_time(e1) / 3
+    del y, gr, S, x, b, G, xt_d
+    torch.cuda.empty_cache()
+    return {"workload": "c2_256: 256^3 volume (40 ellipsoids + 8 inclusions), 360 views, 384x384 detector, "
+                        "log-Poisson data I0=1e4, mini-batch 20 views by the schedule, 20 epochs, FP32",
+            "autotune": tune, "epochs": epochs, "seconds_total": el,
+            "full_sweep": {"forward_ms": t["forward"], "back_ms": t["back"],
+                           "gups_fwd_back": (fwd_u + bp_u) / ((t["forward"] + t["back"]) * 1e-3) / 1e9}}
+
+
+def run_kernels_only(args):
+    """The hot kernels alone, for profiler captures (one GPU; a side mode, not
+    the contract line): the workload's data (ceil(n_views/90) store-mode
+    projector launches), then --steps trial-objective projections of one
+    mini-batch (residual_norm: k_pack, k1_project, k_reduce) and --steps
+    backprojections of it (k_weight, k2_backproject, k_zi_to_natural), in the
+    launch configuration --launch (else the autotuner's, whose timing
+    launches come first).  Prints the CUDA-event time of each."""
+    import torch
+    import paper_2605_12085_gb300 as fbl
+    import synth
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    wl = synth.WORKLOADS[args.workload]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    if args.launch:
+        cols, split, vpl = (int(v) for v in args.launch.split(","))
+        fbl.geometry_set_launch(G, cols, split, vpl)
+        tune = {"k1_cols": cols, "k1_split": split, "k2_vpl": vpl}
+    else:
+        tune = fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    views = fbl.fbl_epoch_batches(wl.seed_batches, 1, g.n_views, wl.N0)[0]
+    x = torch.from_numpy(xt).to(device)
+    y = torch.randn((len(views), g.nv, g.nu), dtype=torch.float32, device=device)
+    gr = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    out = {"workload": args.workload, "views": len(views), "launch": tune}
+    for name, call in (("residual_norm_ms", lambda: fbl.residual_norm(G, x, views, b)),
+                       ("backproject_ms", lambda: fbl.backproject(G, y, views, x=gr))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ts.append(e0.elapsed_time(e1))
+        out[name] = ts
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -809,89 +979,90 @@ def run_ours(args, rank, world, local_rank):
         cols, split, vpl = (int(v) for v in args.launch.split(","))
         fbl.geometry_set_launch(G, cols, split, vpl)
         tune = dict(tune, forced={"k1_cols": cols, "k1_split": split, "k2_vpl": vpl})
-    params = fbl.params_default(alpha0=1e-3, beta=0.5, mu=wl.mu, N0=wl.N0, seed=wl.seed_batches,
-                                max_backtracks=60)
-    S = fbl.fblisa_create(G, params)
-    x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+    peaks, peak_src = load_peaks()
     stream = torch.cuda.current_stream(device)
+
+    # --- the contract's timed region: K full sweeps, forward then back ------
+    views = list(range(g.n_views))
+    xd = torch.from_numpy(xt).to(device)
+    y = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32, device=device)
+    gr = torch.empty(g.vol_shape, dtype=torch.float32, device=device)
     for _ in range(args.warmup):
-        S.step(x, b)
-    S.profile(True)
+        fbl.project(G, xd, views, y=y)
+        fbl.backproject(G, y, views, x=gr)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize(device)
     clocks = ClockSampler(local_rank)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    stats, batches = [], []
-    for _ in range(args.steps):
-        stats.append(S.step(x, b))
-        batches.append(S.last_batch())
+    for a, m, c in ev:
+        a.record(stream)
+        fbl.project(G, xd, views, y=y)
+        m.record(stream)
+        fbl.backproject(G, y, views, x=gr)
+        c.record(stream)
     t1.record(stream)
     torch.cuda.synchronize(device)
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
-    prof = S.profile(False)
-    units = sum(step_units(st, g) for st in stats)
+    fwd_ms = statistics.mean(a.elapsed_time(m) for a, m, _ in ev)
+    bp_ms = statistics.mean(m.elapsed_time(c) for _, m, c in ev)
+    fwd_u, bp_u = sweep_units(g)
+    units = args.steps * (fwd_u + bp_u)
     ms_max, units_all = aggregate_ranks(ms, units, dist)
     value = units_all / (ms_max * 1e-3) / 1e9
-
-    # dominant kernel: the trial-objective projection (K1')
-    peaks, peak_src = load_peaks()
-    k1_ms, k1_n = prof["objective_projection"]
-    samples_per_launch = float(np.mean([active_samples(g, vs) for vs in batches[:3]]))
-    k1_avg_ms = k1_ms / max(k1_n, 1)
-    sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_clock * 1e6 / 1e12  # FP32 lanes x clock, Tops/s
-    achieved = (OPS_PER_SAMPLE * samples_per_launch / (k1_avg_ms * 1e-3) / 1e12
-                if k1_n else None)
-    roofline = {"kernel": "k1_project (trial objective, Step 2c)", "bound": "alu",
-                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": (achieved / alu_peak) if achieved else None,
-                "traffic": k1_traffic(wl.name),
-                "algorithmic_bytes": g.n_vox * 4 + stats[0]["N_t"] * g.nu * g.nv * 4,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock seen)"
-                               % sm_clock,
-                "ops_per_sample": OPS_PER_SAMPLE, "samples_per_launch": samples_per_launch,
-                "avg_launch_ms": k1_avg_ms}
-    k3_ms, k3_n = prof["prox_reduce"]
-    k3_avg = k3_ms / max(k3_n, 1)
-    k3_gbs = K3_BYTES_PER_VOXEL * g.n_vox / (k3_avg * 1e-3) / 1e9 if k3_n else None
-    kernels = {name: {"ms": round(v[0], 3), "launches": v[1]} for name, v in prof.items()}
-    gpu_launches = int(sum(v[1] for v in prof.values()))
-
+    in_vol = float(active_samples(g, views))
+    sweep = {"forward_ms": fwd_ms, "back_ms": bp_ms,
+             "gups_forward": fwd_u / (fwd_ms * 1e-3) / 1e9, "gups_back": bp_u / (bp_ms * 1e-3) / 1e9,
+             "gups_fwd_back": (fwd_u + bp_u) / ((fwd_ms + bp_ms) * 1e-3) / 1e9,
+             "in_volume_samples": in_vol, "nominal_samples": fwd_u,
+             "gsamples_in_volume_forward": in_vol / (fwd_ms * 1e-3) / 1e9,
+             "units": "forward: n_views*nu*nv*N ray samples (nominal; in-volume ones beside); "
+                      "back: n_views*N^3 voxel-views"}
+    # dominant kernel of the step: the backprojection of all views (one K2 launch;
+    # the call's events also hold its short weighting and reordering kernels)
+    bp_bytes = g.n_views * g.nu * (g.nv + 16) * 4 + g.n_vox * 4
+    k2 = alu_roofline("k2_backproject over all %d views (one launch; the timed call also holds "
+                      "k_weight and k_zi_to_natural)" % g.n_views, K2_OPS_PER_SAMPLE, in_vol, bp_ms,
+                      bp_bytes, clk, peaks, voxel_views_per_launch=bp_u)
+    k1 = alu_roofline("k1_project, store mode, all %d views (one launch; the timed call also "
+                      "holds k_pack)" % g.n_views, K1_OPS_PER_SAMPLE, in_vol, fwd_ms,
+                      g.n_vox * 4 + g.n_views * g.nu * g.nv * 4, clk, peaks)
+    dominant, other = (k2, k1) if bp_ms >= fwd_ms else (k1, k2)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "%s: %d^3 volume, %d views, %dx%d detector, mini-batch %d views, "
-                                  "FP32 storage, FP32 accumulation, FP64 line-search sums"
-                                  % (wl.name, g.nx, g.n_views, g.nu, g.nv, wl.N0),
-                      "N_t": stats[0]["N_t"], "alpha0": 1e-3, "beta": 0.5, "mu": wl.mu,
-                      "l2": "inputs larger than L2 (volume %.0f MB, data %.0f MB)"
+           "config": {"workload": "%s: %d^3 volume, %d views, %dx%d detector; step = forward projection "
+                                  "of all %d views + backprojection of all %d views (FP32 storage and "
+                                  "accumulation)" % (wl.name, g.nx, g.n_views, g.nu, g.nv, g.n_views,
+                                                     g.n_views),
+                      "l2": "inputs larger than L2 (volume %.0f MB, projections %.0f MB)"
                             % (g.n_vox * 4 / 1e6, g.n_views * g.nu * g.nv * 4 / 1e6),
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "backtracks_per_step": statistics.mean(st["backtracks"] for st in stats),
-           "roofline": roofline,
-           "roofline_k3": {"kernel": "k_prox_zi", "bound": "hbm", "achieved": k3_gbs,
-                           "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                           "frac": (k3_gbs / peaks["hbm_gbs"]) if k3_gbs else None,
-                           "peak_source": peak_src, "bytes_per_voxel": K3_BYTES_PER_VOXEL},
-           "kernels": kernels, "gpu_launches": gpu_launches, "clocks": clk,
-           "autotune": tune}
+           "full_sweep": sweep, "roofline": dominant, "roofline_other": other,
+           "gpu_launches": 5 * args.steps,
+           "gpu_launches_note": "per step: k_pack + k1_project (project call), k_weight + k2_backproject "
+                                "+ k_zi_to_natural (backproject call)",
+           "clocks": clk, "autotune": tune, "peak_source": peak_src}
+    del y, gr
+
+    # --- the whole hot path: one FB-LISA iteration ---------------------------
+    out["fblisa_iteration"] = fblisa_iteration_record(fbl, G, g, wl, b, device, args.iter_steps, 3, peaks)
 
     if rank == 0:
-        out["full_sweep"] = full_sweep(fbl, G, g, x, device)
         out["fdk"] = fdk_record(fbl, G, g, b, xt, device)
         out["regularisers"] = regularisers_record(fbl, G, g, b, xt, device, peaks)
 
     # storage-precision variants (BF16 / FP16 iterates and data, FP32 arithmetic)
     if args.variants:
-        import torch
         variants = {}
         for name, code, td, graph in (("f32_graph", fbl.F32, torch.float32, 1),
                                       ("bf16", fbl.BF16, torch.bfloat16, 0),
@@ -914,11 +1085,14 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize(device)
             vms = v0.elapsed_time(v1)
             uv = sum(step_units(st, g) for st in stv)
-            variants[name] = {"value": uv / (vms * 1e-3) / 1e9, "unit": UNIT,
-                              "ms_per_step": vms / len(stv), "steps": len(stv),
-                              "backtracks_per_step": statistics.mean(st["backtracks"] for st in stv)}
+            variants[name] = {"gups": uv / (vms * 1e-3) / 1e9, "ms_per_iteration": vms / len(stv),
+                              "steps": len(stv),
+                              "backtracks_per_iteration": statistics.mean(st["backtracks"] for st in stv)}
             del Sv, xv, bv
-        out["variants"] = variants
+        out["fblisa_iteration_variants"] = variants
+
+    if args.c2 and rank == 0:
+        out["c2"] = c2_record(fbl, device, peaks)
 
     if args.batched and rank == 0:
         out["batched"] = batched_records(fbl, device)
@@ -934,26 +1108,30 @@ def run_ours(args, rank, world, local_rank):
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,
-                                                     args.tto_check, xt=xt)
+                                                     args.tto_check, xt=xt, decompose=bool(args.tto_decompose))
 
-    # end to end through the same C-ABI call with host (pinned) buffers
+    # end to end: the same step through the same C-ABI calls with host (pinned)
+    # buffers, host<->device copies inside the timed region
     if args.e2e_steps > 0:
-        S2 = fbl.fblisa_create(G, params)
-        xh = torch.zeros(g.vol_shape, dtype=torch.float32).pin_memory()
-        bh = b.cpu().pin_memory()
-        S2.step(xh, bh)
+        xh = torch.from_numpy(xt).pin_memory()
+        yh = torch.empty((g.n_views, g.nv, g.nu), dtype=torch.float32).pin_memory()
+        gh = torch.empty(g.vol_shape, dtype=torch.float32).pin_memory()
+        fbl.project(G, xh, views, y=yh)
+        fbl.backproject(G, yh, views, x=gh)
         torch.cuda.synchronize(device)
         e0 = time.perf_counter()
-        st2 = [S2.step(xh, bh) for _ in range(args.e2e_steps)]
+        for _ in range(args.e2e_steps):
+            fbl.project(G, xh, views, y=yh)
+            fbl.backproject(G, yh, views, x=gh)
         torch.cuda.synchronize(device)
         e_ms = (time.perf_counter() - e0) * 1e3
-        u2 = sum(step_units(st, g) for st in st2)
-        h2d = g.n_vox * 4 + st2[0]["N_t"] * g.nu * g.nv * 4 + st2[0]["N_t"] * 4
-        d2h = g.n_vox * 4 + 40 * (statistics.mean(s["backtracks"] for s in st2) + 1)
-        out["e2e"] = {"value": u2 / (e_ms * 1e-3) / 1e9 * (units_all / units), "unit": UNIT,
-                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                      "ms_per_step": e_ms / args.e2e_steps}
-        del S2, xh, bh
+        h2d = g.n_vox * 4 + g.n_views * g.nu * g.nv * 4 + 2 * g.n_views * 4
+        d2h = g.n_views * g.nu * g.nv * 4 + g.n_vox * 4
+        out["e2e"] = {"value": args.e2e_steps * (fwd_u + bp_u) / (e_ms * 1e-3) / 1e9 * (units_all / units),
+                      "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                      "ms_per_step": e_ms / args.e2e_steps,
+                      "what": "project(x host -> y host) + backproject(y host -> g host) of all views"}
+        del xh, yh, gh
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, xt)
@@ -1038,6 +1216,10 @@ def main():
     if args.tv_only:
         if rank == 0:
             print(json.dumps(run_tv_only(args)), flush=True)
+        return 0
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps(run_kernels_only(args)), flush=True)
         return 0
     if world > 1:
         import torch.distributed as dist

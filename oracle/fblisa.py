@@ -167,6 +167,8 @@ class StepRecord:
     trials: List[Trial]
     alpha: float
     backtracks: int
+    grad_norm2: float = float("nan")   # ||grad f_N(x)||^2
+    alpha_init: float = float("nan")   # the first trial step
 
     @property
     def margin(self) -> float:
@@ -180,12 +182,16 @@ class LineSearchError(RuntimeError):
 
 def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
             alpha_init: Optional[float] = None, replay_alpha: Optional[float] = None,
-            k: int = 0, epoch: int = 0, tv_state: Optional[TVState] = None):
+            k: int = 0, epoch: int = 0, tv_state: Optional[TVState] = None,
+            first_step=None):
     """One iteration of Alg. 1, Steps 2b-2d, on the mini-batch ``views``.
 
     Returns (x_next, StepRecord).  With ``replay_alpha`` the step size is
     imposed instead of searched (the test (2.3) is still evaluated and
-    recorded, so a disagreement shows as a negative margin).
+    recorded, so a disagreement shows as a negative margin).  ``first_step``:
+    a callable (f_N(x), ||grad f_N(x)||^2) -> first trial step, called after
+    Step 2b (the learned proposal, oracle/proposal.py); else ``alpha_init``
+    or alpha_0.
     """
     n_theta = geom.n_views
     N_t = len(views)
@@ -196,9 +202,13 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
     rho0 = float(np.dot(r.ravel(), r.ravel()))
     f_x = 0.5 * scale * rho0
     g = scale * backproject(geom, r, views)
+    g2 = float(np.dot(g.ravel(), g.ravel()))
     alpha = p.alpha0 if alpha_init is None else alpha_init
+    if first_step is not None:
+        alpha = first_step(f_x, g2)
     if replay_alpha is not None:
         alpha = replay_alpha
+    a_first = alpha
     if p.fixed_step:
         # the deterministic FB baseline of Sec. 3 (with the full batch): one
         # forward-backward step at the constant alpha_0, no sufficient-decrease test
@@ -206,7 +216,7 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
         d = xbar - x
         t = Trial(p.alpha0, float("nan"), float(np.dot(g.ravel(), d.ravel())),
                   float(np.dot(d.ravel(), d.ravel())), float("nan"), float("nan"), True)
-        return xbar, StepRecord(k, epoch, N_t, list(views), rho0, f_x, [t], p.alpha0, 0)
+        return xbar, StepRecord(k, epoch, N_t, list(views), rho0, f_x, [t], p.alpha0, 0, g2, p.alpha0)
     trials = []
     for bt in range(p.max_backtracks + 1):
         # Step 2c: forward-backward point and the test (2.3)
@@ -222,7 +232,7 @@ def fb_step(geom, x: np.ndarray, b: np.ndarray, views: Sequence[int], p: Params,
         trials.append(Trial(alpha, rho1, gTd, dd, f_xbar, rhs, ok))
         if ok or replay_alpha is not None:
             # Step 2d: x^(k+1) = x_bar; the next iteration restarts from alpha_0
-            return xbar, StepRecord(k, epoch, N_t, list(views), rho0, f_x, trials, alpha, bt)
+            return xbar, StepRecord(k, epoch, N_t, list(views), rho0, f_x, trials, alpha, bt, g2, a_first)
         alpha *= p.beta
     raise LineSearchError("no step size passed (2.3) within %d backtracks" % p.max_backtracks)
 

@@ -22,6 +22,7 @@ PROJ = ["tests/test_oracle_projector.py"]
 FDK = ["tests/test_oracle_fdk.py"]
 TV = ["tests/test_oracle_tv.py"]
 MLP = ["tests/test_oracle_mlp.py"]
+PROP = ["tests/test_oracle_proposal.py"]
 
 # (oracle file, text, planted replacement, pin files)
 MUTATIONS = {
@@ -93,6 +94,18 @@ MUTATIONS = {
     "adam_bias_m": ("mlp.py", "    m_hat = m / (1.0 - beta1 ** step)", "    m_hat = m", MLP),
     "adam_bias_v": ("mlp.py", "    v_hat = v / (1.0 - beta2 ** step)", "    v_hat = v", MLP),
     "adam_eps_inside": ("mlp.py", "lr * m_hat / (np.sqrt(v_hat) + eps)", "lr * m_hat / np.sqrt(v_hat + eps)", MLP),
+    # learned step proposal (oracle/proposal.py)
+    "prop_base_zero": ("proposal.py", "    base = st.j_prev if st.have_prev else 0", "    base = 0", PROP),
+    "prop_no_half": ("proposal.py", "base + pred + 0.5 - margin", "base + pred - margin", PROP),
+    "prop_grid_extra": ("proposal.py", "    for _ in range(j):\n        a *= beta",
+                        "    for _ in range(j + 1):\n        a *= beta", PROP),
+    "prop_curvature_no_2": ("proposal.py", "alpha0 * g2 / max(2.0 * f, 1e-300)", "alpha0 * g2 / max(f, 1e-300)", PROP),
+    "prop_grad_ratio_no_sqrt": ("proposal.py", "        out[2] = 0.5 * math.log(", "        out[2] = math.log(", PROP),
+    "prop_absolute_f": ("proposal.py", "        out[1] = math.log(max(f, 1e-300) / max(st.f_prev, 1e-300))",
+                        "        out[1] = math.log(max(f, 1e-300))", PROP),
+    "prop_dj_after_update": ("proposal.py", "    st.dj_prev = j_acc - st.j_prev\n    st.have_dj = st.have_prev\n    st.j_prev = j_acc",
+                             "    st.j_prev = j_acc\n    st.dj_prev = j_acc - st.j_prev\n    st.have_dj = st.have_prev", PROP),
+    "prop_no_k_count": ("proposal.py", "    st.have_prev = True\n    st.k += 1", "    st.have_prev = True", PROP),
 }
 
 
