@@ -14,16 +14,22 @@
 // batch for one band of rows and share a z-slab of the volume in L2.
 //
 // Arithmetic.  Per-ray constants come from the geometry's column tables (FP64
-// on the host, rounded once to Q.40 fixed point): q_b(m) = qb0 + m*qb1 and
+// on the host, rounded once to Q.32 fixed point): q_b(m) = qb0 + m*qb1 and
 // q_z(m) = n*(h0 + m*h1) + cz.  Stepping from plane to plane adds an integer,
-// so every crossing equals its closed form exactly.  Each ray's plane interval
+// so every crossing equals its closed form exactly.  The in-plane crossing is
+// common to a column's rays: it is formed once per plane for the warp, 32
+// planes at a time, into a shared-memory table (plane and row folded into one
+// element offset, and the fraction) that every sample reads with one
+// broadcast load; a sample then costs one 64-bit add and a funnel shift for
+// its vertical crossing, four loads and three interpolations.  Each ray's plane interval
 // [m0, m1] is the exact set of planes whose crossing lies inside
 // (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp walks
 // the union of its rays' intervals -- without per-sample masks where they all
 // overlap, and with masks at the two ends, where a ray outside its own
 // interval samples the zero row k = -1 with weight 0.  Interpolation and the ray sum
-// are FP32; the squared residuals are summed in FP64 across threads and
-// blocks in a fixed order.
+// are FP32 (two partial sums, by the parity of the plane index counted from
+// the warp's first plane); the squared residuals are summed in FP64 across
+// threads and blocks in a fixed order.
 #include <algorithm>
 #include <climits>
 
@@ -65,12 +71,12 @@ __device__ __forceinline__ void clip_affine(float c0, float c1, float lo, float 
     }
 }
 
-// One ray: FP32 constants for the plane-range estimate, exact Q.40 constants
+// One ray: FP32 constants for the plane-range estimate, exact fixed-point constants
 // for the crossings q_b(m) = qb0 + m*qb1 and q_z(m) = qz0 + m*qz1.
 struct RayConst {
     float fqb0, fqb1, fzc0, fzc1, w, cz, Nb, Nz;
     long long qb0, qb1, qz0, qz1;
-    long long hi_b, hi_z;  // Nb and nz in Q.40 (the lower bound is -1)
+    long long hi_b, hi_z;  // Nb and nz in fixed point (the lower bound is -1)
     __device__ __forceinline__ bool inside(int m) const {
         const long long qb = qb0 + (long long)m * qb1;
         const long long qz = qz0 + (long long)m * qz1;
@@ -98,39 +104,45 @@ __device__ __forceinline__ void plane_range(const RayConst &rc, int Na, int &m0,
     m1 = c;
 }
 
-// Plane loop over [m_begin, m_end] for a lane's ray.  MASKED: outside its own
-// interval [o0, o1] the ray samples the zero row k = -1 with weight 0.
+// Planes per in-plane table chunk: one entry per lane.
+constexpr int K1_CHUNK = 32;
+
+// The samples j = 0 .. len-1 of one table chunk for a lane's ray.  tab[j] =
+// (element offset of plane mb + j at in-plane row b0, in-plane fraction fb),
+// shared by the warp's rays (one detector column); qz is the lane's vertical
+// crossing at plane mb (advanced to mb + len).  MASKED: a sample whose plane
+// lies outside the ray's own interval, j outside [r0, r1], reads the zero row
+// k = -1 with weight 0.  Samples with j even go to s0, odd to s1, each in
+// plane order.
 template <bool MASKED, typename TX>
-__device__ __forceinline__ float plane_loop(const TX *__restrict__ vol, int m_begin, int m_end,
-                                            int ps, int bs, int base, const RayConst &rc, int o0,
-                                            int o1) {
-    long long qb = rc.qb0 + (long long)m_begin * rc.qb1;
-    long long qz = rc.qz0 + (long long)m_begin * rc.qz1;
-    int off = base + m_begin * ps;
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll 2
-    for (int m = m_begin; m <= m_end; ++m) {
-        const int b0 = fx_floor(qb);
-        const float fb = fx_frac(qb);
+__device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int2 *__restrict__ tab, int len,
+                                           int bs, long long &qz, long long qz1, int r0, int r1, float &s0,
+                                           float &s1) {
+    auto sample = [&](int j) {
+        const int2 e = tab[j];
         int k0 = fx_floor(qz);
         float fz = fx_frac(qz);
         if (MASKED) {
-            const bool in = (m >= o0) & (m <= o1);
+            const bool in = (unsigned)(j - r0) <= (unsigned)(r1 - r0);
             k0 = in ? k0 : -1;
             fz = in ? fz : 0.f;
         }
-        const TX *p = vol + (off + b0 * bs + k0);
+        qz += qz1;
+        const TX *p = vol + (e.x + k0);
+        const float fb = __int_as_float(e.y);
         const float v00 = ldg_f32(p), v10 = ldg_f32(p + 1);
         const float v01 = ldg_f32(p + bs), v11 = ldg_f32(p + bs + 1);
         const float lo = fmaf(fb, v01 - v00, v00);
         const float hi = fmaf(fb, v11 - v10, v10);
-        const float val = fmaf(fz, hi - lo, lo);
-        if (m & 1) s1 += val; else s0 += val;
-        qb += rc.qb1;
-        qz += rc.qz1;
-        off += ps;
+        return fmaf(fz, hi - lo, lo);
+    };
+    int j = 0;
+#pragma unroll 1
+    for (; j + 1 < len; j += 2) {
+        s0 += sample(j);
+        s1 += sample(j + 1);
     }
-    return s0 + s1;
+    if (j < len) s0 += sample(j);
 }
 
 template <typename TX>
@@ -157,7 +169,7 @@ template <typename TX, typename TB, typename TO, int MODE>
 __device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, int s, int iu, int iv,
                                          float w, float sum, float &r2) {
     const DevGeom &g = a.g;
-    const float W = cB.x * sqrtf(fmaf(w, w, cB.y));
+    const float W = cB.x * sqrtf(fmaf(w, w, cB.y));  // the row weight v_a |d| / |d_a|
     const float ax = W * sum;
     if (MODE == PROJ_STORE) {
         ((TO *)a.out)[((size_t)s * g.nv + iv) * g.nu + iu] = from_f32<TO>(ax);
@@ -174,8 +186,17 @@ __device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, in
 // One block's work: COLS detector columns (block column cb) of batch slot s,
 // detector rows band*32 .. band*32+31; the block's FP64 sum of squared
 // residuals goes to *partial (modes RESID and NORM).  Called by every thread.
+//
+// The warp walks the union [u0, u1] of its rays' plane intervals in chunks
+// of K1_CHUNK planes.  For a chunk, lane l forms the entry of plane mb + l:
+// the in-plane crossing q_b is common to the column's rays, so its floor
+// (folded with the plane into an element offset) and fraction are computed
+// once per plane for the whole warp and read back by every sample with one
+// broadcast shared-memory load.  SPLIT: chunks inside the common part [c0, c1]
+// of the intervals run without per-sample masks.
 template <typename TX, typename TB, typename TO, int MODE, int COLS, bool SPLIT>
 __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int band, double *partial) {
+    __shared__ int2 tab_all[COLS][K1_CHUNK];
     const DevGeom &g = a.g;
     const int lane = threadIdx.x;
     const int iu = cb * COLS + threadIdx.y;  // uniform over the warp
@@ -214,16 +235,32 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
             const int bs = L.inplane_stride(famY);  // next in-plane voxel
             // element (b, m, k) = vol + [PL + (m+1)*ps + (b+1)*bs + k]
             const int base = L.PL + ps + bs;
-            const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
-            if (SPLIT && c0 <= c1) {
-                if (u0 < c0) acc += plane_loop<true, TX>(vol, u0, c0 - 1, ps, bs, base, rc, o0, o1);
-                acc += plane_loop<false, TX>(vol, c0, c1, ps, bs, base, rc, o0, o1);
-                if (c1 < u1) acc += plane_loop<true, TX>(vol, c1 + 1, u1, ps, bs, base, rc, o0, o1);
-            } else {
-                acc = plane_loop<true, TX>(vol, u0, u1, ps, bs, base, rc, o0, o1);
+            int2 *tab = tab_all[threadIdx.y];
+            // the ray's own interval (a ray without samples reads zeros anyway)
+            const int o0 = has ? m0 : u0, o1 = has ? m1 : u1;
+            long long qz = rc.qz0 + (long long)u0 * rc.qz1;
+            float s0 = 0.f, s1 = 0.f;
+            for (int mb = u0; mb <= u1; mb += K1_CHUNK) {
+                const int len = min(K1_CHUNK, u1 - mb + 1);
+                {
+                    const int m = min(mb + lane, u1);
+                    const long long qb = rc.qb0 + (long long)m * rc.qb1;
+                    tab[lane] = make_int2(base + m * ps + fx_floor(qb) * bs, __float_as_int(fx_frac(qb)));
+                }
+                __syncwarp();
+                if (SPLIT && mb >= c0 && mb + len - 1 <= c1)
+                    chunk_loop<false, TX>(vol, tab, len, bs, qz, rc.qz1, 0, 0, s0, s1);
+                else
+                    chunk_loop<true, TX>(vol, tab, len, bs, qz, rc.qz1, o0 - mb, o1 - mb, s0, s1);
+                __syncwarp();
             }
+            acc = s0 + s1;
         }
-        if (iv < g.nv) epilogue<TX, TB, TO, MODE>(a, cB, s, iu, iv, rc.w, acc, r2);
+        // the column's weight constants and the row offset, reloaded rather than
+        // kept live through the plane loop
+        if (iv < g.nv)
+            epilogue<TX, TB, TO, MODE>(a, g.colB[(size_t)a.views[s] * g.nu + iu], s, iu, iv,
+                                       (float)(2 * iv - (g.nv - 1)) * (0.5f * g.dv), acc, r2);
     }
     if (MODE != PROJ_STORE) {
         float vv[1] = {r2};
@@ -254,7 +291,7 @@ __global__ void __launch_bounds__(32 * COLS, 48 / COLS) k1_project(const ProjArg
 // bilinear footprint of the chunk (KZ voxels along z x TMA_KB in-plane rows x
 // TMA_P planes) into one of two buffers while the block samples the previous
 // chunk.  The brick's origin comes from the band's extreme rays of each
-// column, whose crossings are affine in the plane index (exact Q.40), so it
+// column, whose crossings are affine in the plane index (exact fixed point), so it
 // is exact; its z origin is rounded down to the 16-byte rule of TMA.  Every
 // sample still checks its indices against the brick and reads the global
 // copy when outside (and so do chunks whose footprint is larger than a brick,
@@ -523,7 +560,8 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
                 const float hi = fmaf(fb, v11 - v10, v10);
                 val = fmaf(fz, hi - lo, lo);
             }
-            if (m & 1) s1 += val; else s0 += val;
+            // the same partition of the sum as k1_tile: by the parity of m - u0
+            if ((m - u0) & 1) s1 += val; else s0 += val;
             qb += rc.qb1;
             qz += rc.qz1;
         }

@@ -7,7 +7,12 @@ configuration the benchmark times (one 40-view mini-batch per call):
 * the dot test of the two GPU operators at full size;
 * one FB-LISA iteration: the mini-batch equals the oracle's and the accepted
   step satisfies F_N(x_bar) <= F_N(x) - ||d||^2/(2 alpha) (from (2.3) and the
-  prox optimality (A3)).
+  prox optimality (A3));
+* the sums the line search decides on, in the autotuned launch configuration:
+  rho0 = ||A_N x - b_N||^2 from the residual projection (Step 2b) and rho1 from
+  the trial-objective projection (Step 2c), against the oracle's FP64 sums
+  (relative 2e-5), at this workload and at the paper-shaped 560^3 / 840^2 /
+  36-view geometry (Sec. 3, cases 1-2).
 """
 import numpy as np
 import pytest
@@ -101,3 +106,44 @@ def test_fullsize_step_decrease_property(setup):
         assert lhs <= rhs + 1e-6 * abs(rhs)
         assert st["margin"] >= 0
         prev_l1 = l1
+
+
+def _scalar_parity(fbl, wl, x_true, seed):
+    """rho0 of the solver's first iteration and rho1 of residual_norm, both on
+    x0 = x_true/2 with data b = A x_true + 1% noise on the first mini-batch
+    (the oracle's projection; the other views are never read), against the
+    oracle's FP64 sum; the launch configuration is the autotuner's."""
+    import torch
+    g = wl.geom
+    G = fbl.geometry_create(g)
+    tune = fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    views = fblisa.epoch_batches(wl.seed_batches, 1, g.n_views, wl.N0)[0]
+    clean = oracle.project(g, x_true.astype(np.float64), views)
+    noise = synth.gaussian_noise(clean.shape, 0.01 * float(clean.max()), seed, dtype=np.float64)
+    b = np.zeros((g.n_views, g.nv, g.nu), np.float32)
+    b[views] = (clean + noise).astype(np.float32)
+    x0 = (0.5 * x_true).astype(np.float32)
+    r = oracle.project(g, x0.astype(np.float64), views) - b[views].astype(np.float64)
+    rho_ref = float(np.dot(r.ravel(), r.ravel()))
+    bd = torch.from_numpy(b).cuda()
+    S = fbl.fblisa_create(G, fbl.params_default(N0=wl.N0, seed=wl.seed_batches, mu=wl.mu))
+    st = S.step(torch.from_numpy(x0).cuda(), bd)
+    assert S.last_batch() == list(views)
+    rho1 = fbl.residual_norm(G, torch.from_numpy(x0).cuda(), views, bd)
+    return tune, st["rho0"], rho1, rho_ref
+
+
+def test_fullsize_line_search_sums_match_oracle(setup):
+    fbl, G, x, xd, views = setup
+    tune, rho0, rho1, ref = _scalar_parity(fbl, WL, x, 2101)
+    assert rho0 == pytest.approx(ref, rel=2e-5), tune
+    assert rho1 == pytest.approx(ref, rel=2e-5), tune
+
+
+def test_paper_case_geometry_line_search_sums_match_oracle():
+    import paper_2605_12085_gb300 as fbl
+    wl = synth.WORKLOADS["case2_560"]
+    x = synth.phantom(wl.geom, wl.n_ellipsoids, wl.seed_phantom, texture_std=wl.texture_std)
+    tune, rho0, rho1, ref = _scalar_parity(fbl, wl, x, 2102)
+    assert rho0 == pytest.approx(ref, rel=2e-5), tune
+    assert rho1 == pytest.approx(ref, rel=2e-5), tune
