@@ -87,25 +87,34 @@ __host__ __device__ inline int rt_pitch(int nv) { return nv + 2 * RT_PAD; }
 //   wa, h2    row weight v_a*|d|/|d_a| = wa*sqrt(h2 + w^2)
 // ---------------------------------------------------------------------------
 // Crossing positions are exact fixed-point numbers with FX_BITS fractional
-// bits held in int64 (Q.32): stepping from plane to plane adds an integer, so
-// every crossing equals its closed form exactly, K1 and K2 compute identical
+// bits held in int64 (Q.40): stepping from plane to plane adds an integer, so
+// every crossing equals its closed form exactly, K1 and K2 compute the same
 // positions, and the bilinear weights carry full FP32 precision whatever the
 // volume size (an FP32 coordinate near 512 would only resolve 3e-5 voxel).
-// With 32 fractional bits the integer part is the high word and the
-// fraction is one funnel shift of the low word.
-constexpr int FX_BITS = 32;
-constexpr double FX_ONE = 4294967296.0;  // 2^32
+constexpr int FX_BITS = 40;
+constexpr double FX_ONE = 1099511627776.0;  // 2^40
 
 __host__ __device__ __forceinline__ int fx_floor(long long q) { return (int)(q >> FX_BITS); }
-// Fractional part in [0, 1) to 23 bits, as an FP32 number: the low word's top
-// 23 bits become the mantissa of a number in [1, 2) (exponent bits 0x7F).
+// Fractional part in [0, 1) to 23 bits, as an FP32 number.
 __device__ __forceinline__ float fx_frac(long long q) {
+    const unsigned bits = (unsigned)((unsigned long long)q >> (FX_BITS - 23)) & 0x7FFFFFu;
+    return __uint_as_float(bits | 0x3F800000u) - 1.0f;
+}
+
+// The projector's per-sample vertical crossing steps in Q.32: one ray's
+// Q.40 start and step rounded once to 32 fractional bits (so the position
+// after j planes is within (1 + j) 2^-33 voxel of the Q.40 one), whose
+// integer part is the high word and whose fraction is one funnel shift.
+__host__ __device__ __forceinline__ long long fx40_to_32(long long q) { return (q + (1LL << 7)) >> 8; }
+__device__ __forceinline__ int fx32_floor(long long q) { return (int)(q >> 32); }
+__device__ __forceinline__ float fx32_frac(long long q) {
+    // the low word's top 23 bits as the mantissa of a number in [1, 2)
     return __uint_as_float(__funnelshift_r((unsigned)(unsigned long long)q, 0x7Fu, 9)) - 1.0f;
 }
 
 // Fixed-point column constants: q_b(m) = qb0 + m*qb1 and, for the detector
 // row iv with n = 2*iv - (nv-1) (so that w = n*dv/2),
-// q_z(m) = n*(h0 + m*h1) + cz, all in fixed point (FX_BITS).
+// q_z(m) = n*(h0 + m*h1) + cz, all in Q.40.
 struct FxCol {
     long long qb0, qb1, h0, h1;
 };
@@ -122,7 +131,7 @@ struct DevGeom {
     int k1_cols;                 // projector: detector columns per block (4 or 8)
     int k1_split;                // projector plane loop: 0 masked, 1 unmasked middle phase, 2 TMA-staged bricks
     int k2_vpl;                  // backprojector: consecutive voxels per lane (2, 4, 8 or 16)
-    long long cz_fx;             // cz in fixed point (FX_BITS)
+    long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates
     const FxCol *colF;           // [n_views][nu] exact fixed-point constants
     const float4 *colB;          // [n_views][nu] (wa, h2, fam, 0)

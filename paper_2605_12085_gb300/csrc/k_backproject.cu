@@ -13,11 +13,11 @@
 // setup below is paid once per lane for VPL voxels).  Everything that depends only on
 // (i, j) and the view -- the candidate columns within hwu of the voxel
 // column's projection, each column's family, plane m, exact in-plane weight
-// wb (from the same fixed-point crossing K1 uses) and vertical step -- is uniform
+// wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
 // over the warp.  Per voxel, the detector rows that can reach it lie among the
 // ntap rows starting at the first row of its vertical footprint.  For a
 // lane's first voxel the offset q_z - k of that row is taken exactly from the
-// fixed-point crossing; the next rows follow by the per-row step, and the next voxel
+// Q.40 crossing; the next rows follow by the per-row step, and the next voxel
 // by subtracting one and dropping the rows that fell below its footprint, so
 // wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  A column whose rows
 // are spaced by `step` voxels reaches a voxel with at most
@@ -126,7 +126,7 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
     const int nsel = i < g.nx ? a.n_sel : 0;  // a warp past the volume edge only joins the block sum
     const int lo_max = g.nv + RT_PAD - NTAP;  // last first-row whose taps stay in the pad
     const long long kfirst_fx = (long long)kfirst << FX_BITS;
-    constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24: fixed point shifted down to 24 bits
+    constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
     for (int s = 0; s < nsel; ++s) {
         const int v = a.views[s];
         const float2 cs = g.trig[v];
@@ -146,16 +146,16 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
             const float fb = fx_frac(qb);
             const float wb = (b0 == bb) ? 1.f - fb : ((b0 + 1 == bb) ? fb : 0.f);
             if (wb == 0.f) continue;
-            // row iv crosses plane m at q_z = 2*iv*Z + zoff (fixed point), 0 < Z < 2^FX_BITS
+            // row iv crosses plane m at q_z = 2*iv*Z + zoff (Q.40), 0 < Z < 2^40
             const long long Z = cF.h0 + (long long)m * cF.h1;
             const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;
-            const float step = (float)(int)(Z >> (FX_BITS - 25)) * kInv24;  // dq_z per row = 2Z (32-bit path)
+            const float step = (float)(int)(Z >> 15) * kInv24;  // dq_z per row = 2Z (32-bit path)
             const float inv = __fdividef(1.f, step);            // rows per voxel (estimate)
             const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * step;
             // first row whose crossing lies above kfirst - 1: estimate, then one exact correction
             int lo = (int)ceilf(((float)kfirst - zoff_f) * inv - inv);
             const long long d_fx = 2LL * lo * Z + zoff - kfirst_fx;
-            float d0 = (float)(int)(d_fx >> (FX_BITS - 24)) * kInv24;  // q_z(lo) - kfirst (|.| < 2 + step)
+            float d0 = (float)(int)(d_fx >> 16) * kInv24;  // q_z(lo) - kfirst (|.| < 2 + step)
             if (d0 <= -1.f) {
                 ++lo;
                 d0 += step;

@@ -110,7 +110,7 @@ constexpr int K1_CHUNK = 32;
 // The samples j = 0 .. len-1 of one table chunk for a lane's ray.  tab[j] =
 // (element offset of plane mb + j at in-plane row b0, in-plane fraction fb),
 // shared by the warp's rays (one detector column); qz is the lane's vertical
-// crossing at plane mb (advanced to mb + len).  MASKED: a sample whose plane
+// crossing at plane mb in Q.32 (advanced to mb + len).  MASKED: a sample whose plane
 // lies outside the ray's own interval, j outside [r0, r1], reads the zero row
 // k = -1 with weight 0.  Samples with j even go to s0, odd to s1, each in
 // plane order.
@@ -120,8 +120,8 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
                                            float &s1) {
     auto sample = [&](int j) {
         const int2 e = tab[j];
-        int k0 = fx_floor(qz);
-        float fz = fx_frac(qz);
+        int k0 = fx32_floor(qz);
+        float fz = fx32_frac(qz);
         if (MASKED) {
             const bool in = (unsigned)(j - r0) <= (unsigned)(r1 - r0);
             k0 = in ? k0 : -1;
@@ -143,6 +143,14 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
         s1 += sample(j + 1);
     }
     if (j < len) s0 += sample(j);
+}
+
+// The Q.32 line a ray's samples follow from the warp's first plane u0:
+// q_z(u0) and the step rounded once from Q.40, so the sample at plane m sits
+// at qz + (m - u0) qz1, within (1 + m - u0) 2^-33 voxel of the Q.40 crossing.
+__device__ __forceinline__ void ray_z32(const RayConst &rc, int u0, long long &qz, long long &qz1) {
+    qz = fx40_to_32(rc.qz0 + (long long)u0 * rc.qz1);
+    qz1 = fx40_to_32(rc.qz1);
 }
 
 template <typename TX>
@@ -238,7 +246,9 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
             int2 *tab = tab_all[threadIdx.y];
             // the ray's own interval (a ray without samples reads zeros anyway)
             const int o0 = has ? m0 : u0, o1 = has ? m1 : u1;
-            long long qz = rc.qz0 + (long long)u0 * rc.qz1;
+            // the vertical crossing in Q.32 from the warp's first plane (ray_z32)
+            long long qz, qz1;
+            ray_z32(rc, u0, qz, qz1);
             float s0 = 0.f, s1 = 0.f;
             for (int mb = u0; mb <= u1; mb += K1_CHUNK) {
                 const int len = min(K1_CHUNK, u1 - mb + 1);
@@ -249,9 +259,9 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
                 }
                 __syncwarp();
                 if (SPLIT && mb >= c0 && mb + len - 1 <= c1)
-                    chunk_loop<false, TX>(vol, tab, len, bs, qz, rc.qz1, 0, 0, s0, s1);
+                    chunk_loop<false, TX>(vol, tab, len, bs, qz, qz1, 0, 0, s0, s1);
                 else
-                    chunk_loop<true, TX>(vol, tab, len, bs, qz, rc.qz1, o0 - mb, o1 - mb, s0, s1);
+                    chunk_loop<true, TX>(vol, tab, len, bs, qz, qz1, o0 - mb, o1 - mb, s0, s1);
                 __syncwarp();
             }
             acc = s0 + s1;
@@ -461,6 +471,9 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
     const int U0 = s_U0, U1 = s_U1;
     const int nch = U1 >= U0 ? (U1 - U0 + P) / P : 0;
     const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
+    // the lane's vertical crossing on k1_tile's Q.32 line from the warp's first plane
+    long long qz32_u0 = 0, qz1_32 = 0;
+    if (u0 <= u1) ray_z32(rc, u0, qz32_u0, qz1_32);
 
     // produce chunk c into buffer c & 1 (one warp; lanes 0..7 take a column each)
     auto produce = [&](int c) {
@@ -533,12 +546,12 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
         const TX *br = bricks + q * BRICK;
         const int bstride = famY ? KZ : P * KZ;
         long long qb = rc.qb0 + (long long)pa * rc.qb1;
-        long long qz = rc.qz0 + (long long)pa * rc.qz1;
+        long long qz = qz32_u0 + (long long)(pa - u0) * qz1_32;
         for (int m = pa; m <= pb; ++m) {
             const int b0 = fx_floor(qb);
             const float fb = fx_frac(qb);
-            const int k0 = fx_floor(qz);
-            const float fz = fx_frac(qz);
+            const int k0 = fx32_floor(qz);
+            const float fz = fx32_frac(qz);
             float val = 0.f;
             if (m >= o0 && m <= o1) {
                 float v00, v10, v01, v11;
@@ -563,7 +576,7 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
             // the same partition of the sum as k1_tile: by the parity of m - u0
             if ((m - u0) & 1) s1 += val; else s0 += val;
             qb += rc.qb1;
-            qz += rc.qz1;
+            qz += qz1_32;
         }
     }
     // drain: every copy this block issued has landed before shared memory is released
