@@ -612,10 +612,8 @@ extern "C" fbl_status backproject(const fbl_geometry *g, const void *y, int32_t 
         CK(launch_weight(g->dg, yd, y_dtype, (const int32_t *)dviews.p, n_sel, (float *)rt.p, s),
            "weight kernel");
         CK(gz.alloc(nvox * sizeof(float), s), "gradient scratch");
-        AsyncBuf rq;
-        if (g->dg.ntap <= 4) CK(rq.alloc(quad_rows_elems(g->dg, n_sel) * sizeof(float4), s), "quad-row scratch");
         CK(launch_backproject(g->dg, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f,
-                              (float *)gz.p, s, nullptr, (float4 *)rq.p),
+                              (float *)gz.p, s),
            "backproject kernel");
         CK(launch_zi_to_natural((const float *)gz.p, xd, d.nx, d.ny, d.nz, accumulate, s), "reorder");
     }
@@ -884,7 +882,6 @@ struct fbl_solver {
     float *grad = nullptr;              // gradient, [j][i][k]
     float *rt = nullptr;                // weighted residual rt[s][iu][RT_PAD + iv]
     size_t rt_cap = 0;
-    float4 *rq = nullptr;               // its quad-row copy for the backprojector (NULL: not used)
     void *bstage = nullptr;
     size_t bstage_cap = 0;
     void *xstage = nullptr;
@@ -951,7 +948,6 @@ void solver_free(fbl_solver *s) {
     cudaFree(s->grad);
     cudaFree(s->tv_buf);
     cudaFree(s->rt);
-    cudaFree(s->rq);
     cudaFree(s->bstage);
     cudaFree(s->xstage);
     cudaFree(s->d_views);
@@ -1017,13 +1013,10 @@ fbl_status ensure_batch_buffers(fbl_solver *s, int32_t N) {
     if (need > s->rt_cap) {
         drop_graphs(s);  // captured graphs hold the old addresses
         cudaFree(s->rt);
-        cudaFree(s->rq);
         s->rt = nullptr;
-        s->rq = nullptr;
         s->rt_cap = 0;
         CK(cudaMalloc(&s->rt, need * sizeof(float)), "residual buffer");
         CK(cudaMemset(s->rt, 0, need * sizeof(float)), "residual buffer");  // zero row pads
-        if (s->dg.ntap <= 4) CK(cudaMalloc(&s->rq, need * sizeof(float4)), "quad-row buffer");
         s->rt_cap = need;
     }
     const size_t np = std::max({(size_t)project_num_partials(s->dg, N),
@@ -1070,7 +1063,7 @@ fbl_status build_graph(fbl_solver *s, fbl_solver::GraphEntry &ge) {
     cudaError_t e = launch_project(PROJ_RESID, s->dg, ge.st, s->L, xdt, s->d_views, N, ge.bd,
                                    s->p.b_dtype, ge.bmap, s->rt, FBL_F32, s->partials, &np, cs);
     if (e == cudaSuccess) e = launch_reduce(s->partials, np, np, 1, s->d_sc + 0, cs);
-    if (e == cudaSuccess) e = launch_backproject(s->dg, s->rt, s->d_views, N, scale, s->grad, cs, s->partials, s->rq);
+    if (e == cudaSuccess) e = launch_backproject(s->dg, s->rt, s->d_views, N, scale, s->grad, cs, s->partials);
     const int nbp = backproject_num_partials(s->dg);
     if (e == cudaSuccess) e = launch_reduce(s->partials, nbp, nbp, 1, s->d_sc + 5, cs);
     if (e == cudaSuccess) e = launch_propose(s->d_ls, s->d_ps, s->d_sc, s->p.proposal ? s->d_mlp : nullptr, s->margin, cs);
@@ -1188,7 +1181,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
         CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
            "reduce");
         CK(prof_launch(s, 2, st, [&] {
-               return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials, s->rq);
+               return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials);
            }),
            "gradient kernel");
         const int nbp = backproject_num_partials(s->dg);
@@ -1320,7 +1313,7 @@ fbl_status solver_iterate(fbl_solver *s, const void *b, bool b_dev, fbl_step_sta
     CK(prof_launch(s, 4, st, [&] { return launch_reduce(s->partials, np, np, 1, s->d_sc + 0, st); }),
        "reduce");
     CK(prof_launch(s, 2, st, [&] {
-           return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials, s->rq);
+           return launch_backproject(s->dg, s->rt, s->d_views, N, (float)scale, s->grad, st, s->partials);
        }),
        "gradient kernel");
     const int nbp = backproject_num_partials(s->dg);
@@ -1487,9 +1480,8 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
     const size_t nvox = (size_t)d.nx * d.ny * d.nz;
     const size_t bel = (size_t)n_sel * d.nv * d.nu;
     const size_t rtel = (size_t)n_sel * d.nu * rt_pitch(d.nv);
-    AsyncBuf vol, b, rt, rq, gz, part, dviews;
+    AsyncBuf vol, b, rt, gz, part, dviews;
     CK(vol.alloc(vbytes, st), "autotune");
-    if (dg.ntap <= 4) CK(rq.alloc(quad_rows_elems(dg, n_sel) * sizeof(float4), st), "autotune");
     CK(cudaMemsetAsync(vol.p, 0x3c, vbytes, st), "autotune");
     CK(b.alloc(bel * sizeof(float), st), "autotune");
     CK(cudaMemsetAsync(b.p, 0, bel * sizeof(float), st), "autotune");
@@ -1566,7 +1558,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
         cudaError_t e = time_it(
             [&] {
                 return launch_backproject(t, (const float *)rt.p, (const int32_t *)dviews.p, n_sel, 1.0f,
-                                          (float *)gz.p, st, nullptr, (float4 *)rq.p);
+                                          (float *)gz.p, st);
             },
             ms);
         if (e != cudaSuccess) {

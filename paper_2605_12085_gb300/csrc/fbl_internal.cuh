@@ -170,14 +170,9 @@ cudaError_t launch_weight(const DevGeom &g, const void *y, int y_dtype, const in
 
 // gzi[j][i][k] = scale * sum over listed views of the transpose taps of rt;
 // with g2_partials, also the per-block sums of gzi^2 (backproject_num_partials).
-// rq (optional scratch of quad_rows_elems float4): when given and the
-// geometry needs at most 4 taps per voxel and column, rt is first copied to
-// quad rows there and the taps read one 16-byte entry each (same sums).
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
                                int n_sel, float scale, float *gzi, cudaStream_t st,
-                               double *g2_partials = nullptr, float4 *rq = nullptr);
-// float4 entries of the quad-row scratch for n_sel views
-inline size_t quad_rows_elems(const DevGeom &g, int n_sel) { return (size_t)n_sel * g.nu * rt_pitch(g.nv); }
+                               double *g2_partials = nullptr);
 int backproject_num_partials(const DevGeom &g);
 
 // x_bar = min(max(x - alpha*g - alpha*mu, 0), xmax) on the solver's state:

@@ -43,7 +43,6 @@ constexpr int K2_WARPS = 8;   // consecutive i per block
 struct BpArgs {
     DevGeom g;
     const float *rt;
-    const float4 *rq;     // rq[...][e] = rt[...][e .. e+3] (quad rows), or NULL
     const int32_t *views;
     int n_sel;
     float scale;
@@ -56,39 +55,26 @@ struct BpArgs {
 // voxel (-1 < d0 <= -1 + step).  After each voxel the window drops the rows
 // that fell below the next voxel's footprint.  CLAMP: keep each window inside
 // the zero pads (needed only when a lane's windows could leave them; a window
-// clamped into the pads holds no real row since ntap <= RT_PAD).  QUAD
-// (NT <= 4): the window's rows come in one 16-byte load of the quad-row copy
-// qcol[lo] = (rcol[lo], .., rcol[lo + 3]) instead of NT scattered 4-byte
-// loads; the taps and their order are the same, so are the sums.
-template <int NT, int VPL, bool CLAMP, bool QUAD>
+// clamped into the pads holds no real row since ntap <= RT_PAD).
+template <int NT, int VPL, bool CLAMP>
 __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
-                                            const float4 *__restrict__ qcol, int lo, float d0, float step,
-                                            int lo_max) {
-    static_assert(!QUAD || NT <= 4, "a quad row holds four taps");
+                                            int lo, float d0, float step, int lo_max) {
+    const float *r = rcol + lo;
 #pragma unroll
     for (int q = 0; q < VPL; ++q) {
-        const int w = CLAMP ? min(max(lo, -RT_PAD), lo_max) : lo;
-        float rv[NT];
-        if (QUAD) {
-            const float4 v4 = __ldg(qcol + w);
-            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-            for (int t = 0; t < NT; ++t) rv[t] = v[QUAD ? t : 0];
-        } else {
-#pragma unroll
-            for (int t = 0; t < NT; ++t) rv[t] = __ldg(rcol + w + t);
-        }
+        const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
         float sz = 0.f;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const float d = fmaf((float)t, step, d0);
-            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), rv[t], sz);
+            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(w + t), sz);
         }
         acc[q] = fmaf(wb, sz, acc[q]);
         // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
         d0 -= 1.f;
         while (d0 <= -1.f) {
-            ++lo;
+            if (CLAMP) ++lo;
+            else ++r;
             d0 += step;
         }
     }
@@ -99,33 +85,32 @@ __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const f
 // closest), and the clamp-free form when every lane's windows stay inside the
 // pads (a warp vote; all lanes are active).  A window with more taps than
 // needed gives the same sums (the extra taps weigh exactly 0).
-template <int NTAP, int VPL, bool CLAMP, bool QUAD>
+template <int NTAP, int VPL, bool CLAMP>
 __device__ __forceinline__ void column_taps_nt(int nt, float (&acc)[VPL], float wb,
-                                               const float *__restrict__ rcol, const float4 *__restrict__ qcol,
-                                               int lo, float d0, float step, int lo_max) {
+                                               const float *__restrict__ rcol, int lo, float d0, float step,
+                                               int lo_max) {
     constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
     constexpr int NT2 = NTAP > 2 ? NTAP - 2 : NT1;
-    if (nt <= NT2) column_taps<NT2, VPL, CLAMP, QUAD>(acc, wb, rcol, qcol, lo, d0, step, lo_max);
-    else if (nt <= NT1) column_taps<NT1, VPL, CLAMP, QUAD>(acc, wb, rcol, qcol, lo, d0, step, lo_max);
-    else column_taps<NTAP, VPL, CLAMP, QUAD>(acc, wb, rcol, qcol, lo, d0, step, lo_max);
+    if (nt <= NT2) column_taps<NT2, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+    else if (nt <= NT1) column_taps<NT1, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+    else column_taps<NTAP, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
 }
 
-template <int NTAP, int VPL, bool QUAD>
+template <int NTAP, int VPL>
 __device__ __forceinline__ void column_taps_any(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
-                                                const float4 *__restrict__ qcol, int lo, float d0, float step,
-                                                float inv, int lo_max) {
+                                                int lo, float d0, float step, float inv, int lo_max) {
     const int nt = (int)(2.f * inv * 1.0001f + 0.002f) + 1;
     const bool inside = lo >= -RT_PAD && lo + (int)((float)VPL * inv) + 2 <= lo_max;
     if (__all_sync(0xffffffffu, inside))
-        column_taps_nt<NTAP, VPL, false, QUAD>(nt, acc, wb, rcol, qcol, lo, d0, step, lo_max);
+        column_taps_nt<NTAP, VPL, false>(nt, acc, wb, rcol, lo, d0, step, lo_max);
     else
-        column_taps_nt<NTAP, VPL, true, QUAD>(nt, acc, wb, rcol, qcol, lo, d0, step, lo_max);
+        column_taps_nt<NTAP, VPL, true>(nt, acc, wb, rcol, lo, d0, step, lo_max);
 }
 
 // One block's work: voxel columns i = bx*8 .. bx*8+7 of row j, z-span bz;
 // the block's sum of squared gradient values goes to *g2_partial (if not NULL).
 // Called by every thread.
-template <int NTAP, int K2_VPL, bool QUAD>
+template <int NTAP, int K2_VPL>
 __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, double *g2_partial) {
     constexpr int K2_KSPAN = K2_LANES * K2_VPL;
     const DevGeom &g = a.g;
@@ -178,9 +163,8 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
                 --lo;
                 d0 -= step;
             }
-            const size_t cofs = ((size_t)s * g.nu + iu) * rp + RT_PAD;
-            column_taps_any<NTAP, K2_VPL, QUAD>(acc, wb, a.rt + cofs, QUAD ? a.rq + cofs : nullptr, lo, d0,
-                                                step, inv, lo_max);
+            const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
+            column_taps_any<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, inv, lo_max);
         }
     }
     float g2 = 0.f;
@@ -204,30 +188,13 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
     }
 }
 
-template <int NTAP, int K2_VPL, bool QUAD>
+template <int NTAP, int K2_VPL>
 // At most 48 registers (5 blocks per SM); measured against the compiler's own
 // choices (40, and 92-168 with one block per SM): 14.47 against 14.68 and
 // 18.9 ms per 40-view launch at 512^3 with 8 voxels per lane.
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) k2_backproject(const BpArgs a) {
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    k2_tile<NTAP, K2_VPL, QUAD>(a, blockIdx.x, blockIdx.y, blockIdx.z,
-                                a.g2_partials ? a.g2_partials + blk : nullptr);
-}
-
-// rq[c][e] = (rt[c][e], rt[c][e+1], rt[c][e+2], rt[c][e+3]) for every column c
-// of the batch and every padded row e < rp, entries past the row end zero.
-__global__ void __launch_bounds__(256) k_quad_rows(const float *__restrict__ rt, float4 *__restrict__ rq,
-                                                   int rp, long long n_cols) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_cols * rp) return;
-    const int e = (int)(idx % rp);
-    const float *r = rt + idx;
-    float4 v;
-    v.x = r[0];
-    v.y = e + 1 < rp ? r[1] : 0.f;
-    v.z = e + 2 < rp ? r[2] : 0.f;
-    v.w = e + 3 < rp ? r[3] : 0.f;
-    rq[idx] = v;
+    k2_tile<NTAP, K2_VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
 }
 
 // Persistent batched backprojector: the blocks of k2_backproject of every
@@ -253,7 +220,6 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const Ba
         stage_words(&sa.g, &bv.g, sizeof(DevGeom), tid, K2_LANES * K2_WARPS);
         if (tid == 0) {
             sa.rt = bv.rt;
-            sa.rq = nullptr;
             sa.views = bv.views;
             sa.n_sel = bv.N_t;
             sa.scale = bv.scale;
@@ -271,10 +237,10 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const Ba
         const int bz = rest / bv.g.ny;
         double *part = bv.partials + local;
         switch (vpl) {
-            case 2: k2_tile<NTAP, 2, false>(a, bx, j, bz, part); break;
-            case 8: k2_tile<NTAP, 8, false>(a, bx, j, bz, part); break;
-            case 16: k2_tile<NTAP, 16, false>(a, bx, j, bz, part); break;
-            default: k2_tile<NTAP, 4, false>(a, bx, j, bz, part); break;
+            case 2: k2_tile<NTAP, 2>(a, bx, j, bz, part); break;
+            case 8: k2_tile<NTAP, 8>(a, bx, j, bz, part); break;
+            case 16: k2_tile<NTAP, 16>(a, bx, j, bz, part); break;
+            default: k2_tile<NTAP, 4>(a, bx, j, bz, part); break;
         }
     }
     if (tid == 0) {
@@ -295,13 +261,13 @@ int backproject_num_partials(const DevGeom &g) {
     return ((g.nx + K2_WARPS - 1) / K2_WARPS) * g.ny * ((g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
 }
 
-template <int NT, bool QUAD>
+template <int NT>
 static void launch_k2(int vpl, dim3 grid, dim3 block, cudaStream_t st, const BpArgs &a) {
     switch (vpl) {
-        case 2: k2_backproject<NT, 2, QUAD><<<grid, block, 0, st>>>(a); break;
-        case 8: k2_backproject<NT, 8, QUAD><<<grid, block, 0, st>>>(a); break;
-        case 16: k2_backproject<NT, 16, QUAD><<<grid, block, 0, st>>>(a); break;
-        default: k2_backproject<NT, 4, QUAD><<<grid, block, 0, st>>>(a); break;
+        case 2: k2_backproject<NT, 2><<<grid, block, 0, st>>>(a); break;
+        case 8: k2_backproject<NT, 8><<<grid, block, 0, st>>>(a); break;
+        case 16: k2_backproject<NT, 16><<<grid, block, 0, st>>>(a); break;
+        default: k2_backproject<NT, 4><<<grid, block, 0, st>>>(a); break;
     }
 }
 
@@ -338,12 +304,11 @@ cudaError_t launch_batch_backproject(const BatchHdr *hdr, BatchVol *vols, int nt
 
 cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t *views,
                                int n_sel, float scale, float *gzi, cudaStream_t st,
-                               double *g2_partials, float4 *rq) {
+                               double *g2_partials) {
     BpArgs a;
     a.g2_partials = g2_partials;
     a.g = g;
     a.rt = rt;
-    a.rq = nullptr;
     a.views = views;
     a.n_sel = n_sel;
     a.scale = scale;
@@ -351,30 +316,15 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
     dim3 block(K2_LANES, K2_WARPS);
     const int vpl = k2_vpl_of(g);
     dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
-    if (rq && g.ntap <= 4 && n_sel > 0) {
-        // the quad-row copy of this batch's weighted residual, then the same taps
-        const long long n_cols = (long long)n_sel * g.nu;
-        const int rp = rt_pitch(g.nv);
-        const long long n = n_cols * rp;
-        k_quad_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rt, rq, rp, n_cols);
-        a.rq = rq;
-        switch (g.ntap) {
-            case 1: launch_k2<1, true>(vpl, grid, block, st, a); break;
-            case 2: launch_k2<2, true>(vpl, grid, block, st, a); break;
-            case 3: launch_k2<3, true>(vpl, grid, block, st, a); break;
-            default: launch_k2<4, true>(vpl, grid, block, st, a); break;
-        }
-        return cudaGetLastError();
-    }
     switch (g.ntap) {  // rows per voxel and column, fixed per geometry (<= RT_PAD)
-        case 1: launch_k2<1, false>(vpl, grid, block, st, a); break;
-        case 2: launch_k2<2, false>(vpl, grid, block, st, a); break;
-        case 3: launch_k2<3, false>(vpl, grid, block, st, a); break;
-        case 4: launch_k2<4, false>(vpl, grid, block, st, a); break;
-        case 5: launch_k2<5, false>(vpl, grid, block, st, a); break;
-        case 6: launch_k2<6, false>(vpl, grid, block, st, a); break;
-        case 7: launch_k2<7, false>(vpl, grid, block, st, a); break;
-        default: launch_k2<8, false>(vpl, grid, block, st, a); break;
+        case 1: launch_k2<1>(vpl, grid, block, st, a); break;
+        case 2: launch_k2<2>(vpl, grid, block, st, a); break;
+        case 3: launch_k2<3>(vpl, grid, block, st, a); break;
+        case 4: launch_k2<4>(vpl, grid, block, st, a); break;
+        case 5: launch_k2<5>(vpl, grid, block, st, a); break;
+        case 6: launch_k2<6>(vpl, grid, block, st, a); break;
+        case 7: launch_k2<7>(vpl, grid, block, st, a); break;
+        default: launch_k2<8>(vpl, grid, block, st, a); break;
     }
     return cudaGetLastError();
 }
