@@ -75,6 +75,10 @@ def parse():
                     help="also run the paper's comparison: FB, full-batch and mini-batch FB-LISA (2+ min)")
     ap.add_argument("--paper-cases", type=int, default=0,
                     help="also run the paper-shaped 560^3 cases with RE / PSNR over time (several minutes)")
+    ap.add_argument("--paper-mu-sweep", type=int, default=0,
+                    help="also sweep mu = c * max(A^T b) on the paper-shaped case 2 (about two minutes)")
+    ap.add_argument("--paper-mu-fraction", type=float, default=None,
+                    help="with --paper-cases: mu = (2c, c, c) * max(A^T b) instead of the paper's 2 / 1 / 1")
     ap.add_argument("--c5b", type=int, default=0,
                     help="also time the 1024^3 / 1440-view FP16 configuration (a few minutes more)")
     ap.add_argument("--tv-only", type=int, default=0,
@@ -286,10 +290,63 @@ def comparators_record(fbl, device, budget_s=30.0):
     return out
 
 
-def paper_cases_record(fbl, device, budget_s=30.0):
+def mu_max(fbl, G, g, b):
+    """max_j (A^T b)_j over all views: for R = mu ||x||_1 + indicator{x >= 0},
+    x = 0 minimises (2.1) exactly when mu >= this value, so mu is read as a
+    fraction of it (the paper's mu values belong to its own data scaling)."""
+    return float(fbl.backproject(G, b, list(range(g.n_views))).max())
+
+
+def paper_mu_sweep_record(fbl, device, budget_s=15.0, fractions=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2)):
+    """Case 2 in shape (560^3, 36 views, 2% noise): plain FP32 FB-LISA for
+    budget_s of GPU time at mu = c * max(A^T b) for each fraction c; the final
+    and the best relative error to the phantom, the final F, and the share of
+    zero voxels.  The fraction whose final error is smallest is the reading
+    used for the paper-shaped cases."""
+    import torch
+    import synth
+    wl = synth.WORKLOADS["case2_560"]
+    g = wl.geom
+    G, xt, b = make_data(fbl, wl, device)
+    fbl.geometry_autotune(G, fbl.F32, wl.N0)
+    xt_d = torch.from_numpy(xt).to(device)
+    mmax = mu_max(fbl, G, g, b)
+    stream = torch.cuda.current_stream(device)
+    out = {"workload": "case2_560", "budget_s": budget_s, "mu_max": mmax, "runs": []}
+    for c in fractions:
+        mu = c * mmax
+        S = fbl.fblisa_create(G, fbl.params_default(alpha0=1e-3, beta=0.5, mu=mu, N0=wl.N0, seed=wl.seed_batches))
+        x = torch.zeros(g.vol_shape, dtype=torch.float32, device=device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        el, k, best = 0.0, 0, (float("inf"), 0)
+        while el < budget_s and k < 5000:
+            e0.record(stream)
+            S.step(x, b)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            el += e0.elapsed_time(e1) * 1e-3
+            k += 1
+            if k % 10 == 0:
+                re = float(torch.linalg.vector_norm(x - xt_d) / torch.linalg.vector_norm(xt_d))
+                best = min(best, (re, k))
+        F, _, re = fbl.evaluate(G, x, b, mu, x_true=xt_d)
+        out["runs"].append({"fraction": c, "mu": mu, "iterations": k, "final_rel_error": re, "F": F,
+                            "best_rel_error": min(best[0], re), "best_at_iteration": best[1],
+                            "zero_share": float((x == 0).float().mean())})
+        del S, x
+    out["chosen_fraction"] = min(out["runs"], key=lambda r: r["final_rel_error"])["fraction"]
+    del G, b, xt_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def paper_cases_record(fbl, device, budget_s=30.0, mu_fraction=None):
     """The paper's three cases (Sec. 3) in shape on seeded phantoms (the walnut
     data are not available): 560^3, 36 / 36 / 72 views, 840^2 detector,
-    N_0 = 8, alpha_0 = 1e-3, mu = 2 / 1 / 1.  Each method runs for budget_s of
+    N_0 = 8, alpha_0 = 1e-3, mu = 2 / 1 / 1 -- or, with mu_fraction c, the
+    data-scaled reading mu = (2c, c, c) * max(A^T b) of the case's data, so that
+    the three cases keep the paper's ratio.  Each method runs for budget_s of
     GPU time: plain FB-LISA (FP32), the fast configuration, and constant-step
     FB on the full batch (step 0.9/L).  Reported: RE = ||x - x_true|| /
     ||x_true|| and PSNR = 10 log10(max(x_true)^2 / MSE) at fixed times and at
@@ -302,12 +359,16 @@ def paper_cases_record(fbl, device, budget_s=30.0):
     from paper_2605_12085_gb300 import proposal as prop
     net, _ = prop.load()
     stream = torch.cuda.current_stream(device)
-    out = {"budget_s_per_method": budget_s}
+    out = {"budget_s_per_method": budget_s, "mu_fraction": mu_fraction}
     for case in ("case1_560", "case2_560", "case3_560"):
         wl = synth.WORKLOADS[case]
         g = wl.geom
         G, xt, b = make_data(fbl, wl, device)
         fbl.geometry_autotune(G, fbl.F32, wl.N0)
+        mu = wl.mu
+        if mu_fraction is not None:
+            mmax = mu_max(fbl, G, g, b)
+            mu = (2.0 if case == "case1_560" else 1.0) * mu_fraction * mmax
         xt_d = torch.from_numpy(xt).to(device)
         peak2 = float(xt.max()) ** 2
         xt_n2 = float((xt.astype("float64") ** 2).sum())
@@ -358,7 +419,7 @@ def paper_cases_record(fbl, device, budget_s=30.0):
                 el += e0.elapsed_time(e1) * 1e-3
                 k += 1
                 if k % 10 == 0 or k in (120, 240):
-                    F, _, re = fbl.evaluate(G, x.float(), b, wl.mu, x_true=xt_d)
+                    F, _, re = fbl.evaluate(G, x.float(), b, mu, x_true=xt_d)
                     hist.append((el, k, F, re))
             rec = {"iterations": k, "ms_per_iteration": 1e3 * el / max(k, 1)}
             for t in (budget_s / 4, budget_s / 2, budget_s):
@@ -377,9 +438,9 @@ def paper_cases_record(fbl, device, budget_s=30.0):
                                "seconds": best[0]}
             return rec
 
-        base = dict(beta=0.5, mu=wl.mu, seed=wl.seed_batches)
+        base = dict(beta=0.5, mu=mu, seed=wl.seed_batches)
         out[case] = {
-            "views": g.n_views, "mu": wl.mu, "noise_rel": wl.noise_rel, "L_estimate": L,
+            "views": g.n_views, "mu": mu, "noise_rel": wl.noise_rel, "L_estimate": L,
             "fblisa_fp32": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, **base)),
             "fblisa_fast": run(fbl.params_default(alpha0=1e-3, N0=wl.N0, x_dtype=fbl.BF16, b_dtype=fbl.BF16,
                                                   use_graph=1, proposal=1, **base), fast=True),
@@ -1103,8 +1164,11 @@ def run_ours(args, rank, world, local_rank):
     if args.comparators and rank == 0:
         out["comparators"] = comparators_record(fbl, device)
 
+    if args.paper_mu_sweep and rank == 0:
+        out["paper_mu_sweep"] = paper_mu_sweep_record(fbl, device)
+
     if args.paper_cases and rank == 0:
-        out["paper_cases"] = paper_cases_record(fbl, device)
+        out["paper_cases"] = paper_cases_record(fbl, device, mu_fraction=args.paper_mu_fraction)
 
     if args.tto_epochs > 0 and rank == 0:
         out["time_to_objective"] = time_to_objective(fbl, G, g, wl, b, device, args.tto_epochs,
