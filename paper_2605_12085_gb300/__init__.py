@@ -67,7 +67,7 @@ class fbl_step_stats(ctypes.Structure):
 
 
 class fbl_tune_report(ctypes.Structure):
-    _fields_ = [("k1_ms", ctypes.c_float * 5), ("k2_ms", ctypes.c_float * 4),
+    _fields_ = [("k1_ms", ctypes.c_float * 5), ("k2_ms", ctypes.c_float * 6),
                 ("k1_cols", ctypes.c_int32), ("k1_split", ctypes.c_int32),
                 ("k2_vpl", ctypes.c_int32)]
 

@@ -1551,7 +1551,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
     }
     best = 1e30f;
     qi = 0;
-    for (int vpl : {4, 2, 8, 16}) {
+    for (int vpl : {4, 2, 8, 16, 24, 28}) {
         DevGeom t = dg;
         t.k2_vpl = vpl;
         float ms = 0.f;
@@ -1566,7 +1566,7 @@ fbl_status autotune_devgeom(const fbl_geometry *g, DevGeom &dg, int x_dtype, int
             cudaEventDestroy(e1);
             return cuda_fail(e, "autotune backprojector");
         }
-        if (rep && qi < 4) rep->k2_ms[qi] = ms;
+        if (rep && qi < 6) rep->k2_ms[qi] = ms;
         ++qi;
         if (ms < best) {
             best = ms;
@@ -1646,9 +1646,10 @@ extern "C" fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int3
                                           int32_t k2_vpl) {
     if (!g) return fail(FBL_E_INVAL, "geometry_set_launch: null geometry");
     if ((k1_cols != 4 && k1_cols != 8) || (k1_split < 0 || k1_split > 2) ||
-        (k2_vpl != 2 && k2_vpl != 4 && k2_vpl != 8 && k2_vpl != 16))
+        (k2_vpl != 2 && k2_vpl != 4 && k2_vpl != 8 && k2_vpl != 16 && k2_vpl != 24 && k2_vpl != 28))
         return fail(FBL_E_INVAL,
-                    "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1,2}, k2_vpl in {2,4,8,16}");
+                    "geometry_set_launch: need k1_cols in {4,8}, k1_split in {0,1,2}, "
+                    "k2_vpl in {2,4,8,16,24,28}");
     g->dg.k1_cols = k1_cols;
     g->dg.k1_split = k1_split;
     g->dg.k2_vpl = k2_vpl;
@@ -2179,6 +2180,9 @@ extern "C" fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, cons
         p.use_graph = 0;
         fbl_solver *s = nullptr;
         st = fblisa_create(geoms[v], &p, &s);
+        // the batched backprojector takes one voxel column per warp: a 2x2 group
+        // configuration runs with its voxels per lane (the same sums)
+        if (!st && (s->dg.k2_vpl == 24 || s->dg.k2_vpl == 28)) s->dg.k2_vpl -= 20;
         if (st) {
             std::string keep = g_last_error;
             batch_free(bt);

@@ -35,7 +35,14 @@ namespace {
 
 constexpr int K2_LANES = 32;
 
+// Launch configuration of the backprojector: k2_vpl in {2, 4, 8, 16} is one
+// voxel column per warp with that many consecutive voxels per lane; 24 and 28
+// are a 2x2 group of voxel columns per warp (k2_tile22) with 4 or 8 voxels per
+// lane in each.  The batched kernel runs a group volume with one column per
+// warp and the same voxels per lane (the sums are the same).
+__host__ __device__ __forceinline__ bool k2_group_of(const DevGeom &g) { return g.k2_vpl == 24 || g.k2_vpl == 28; }
 __host__ __device__ __forceinline__ int k2_vpl_of(const DevGeom &g) {
+    if (k2_group_of(g)) return g.k2_vpl - 20;
     return (g.k2_vpl == 2 || g.k2_vpl == 8 || g.k2_vpl == 16) ? g.k2_vpl : 4;
 }
 constexpr int K2_WARPS = 8;   // consecutive i per block
@@ -105,6 +112,191 @@ __device__ __forceinline__ void column_taps_any(float (&acc)[VPL], float wb, con
         column_taps_nt<NTAP, VPL, false>(nt, acc, wb, rcol, lo, d0, step, lo_max);
     else
         column_taps_nt<NTAP, VPL, true>(nt, acc, wb, rcol, lo, d0, step, lo_max);
+}
+
+// column_taps for a z-profile that two voxel columns share: the same window,
+// taps and advance, with sz accumulated into both as fmaf(w, sz, acc) (a zero
+// weight leaves an accumulator's bits unchanged: acc is never -0 and sz is
+// finite).
+template <int NT, int VPL, bool CLAMP>
+__device__ __forceinline__ void column_taps2(float (&accA)[VPL], float (&accB)[VPL], float wA, float wB,
+                                             const float *__restrict__ rcol, int lo, float d0, float step,
+                                             int lo_max) {
+    const float *r = rcol + lo;
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+        const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
+        float sz = 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const float d = fmaf((float)t, step, d0);
+            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(w + t), sz);
+        }
+        accA[q] = fmaf(wA, sz, accA[q]);
+        accB[q] = fmaf(wB, sz, accB[q]);
+        d0 -= 1.f;
+        while (d0 <= -1.f) {
+            if (CLAMP) ++lo;
+            else ++r;
+            d0 += step;
+        }
+    }
+}
+
+template <int NTAP, int VPL, bool CLAMP>
+__device__ __forceinline__ void column_taps2_nt(int nt, float (&accA)[VPL], float (&accB)[VPL], float wA, float wB,
+                                                const float *__restrict__ rcol, int lo, float d0, float step,
+                                                int lo_max) {
+    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
+    constexpr int NT2 = NTAP > 2 ? NTAP - 2 : NT1;
+    if (nt <= NT2) column_taps2<NT2, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
+    else if (nt <= NT1) column_taps2<NT1, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
+    else column_taps2<NTAP, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
+}
+
+// The first row of one (column, plane) window for the lane's first voxel:
+// lo and d0 = q_z(lo) - kfirst in (-1, -1 + step], exact from the Q.40
+// crossing (an FP32 estimate and one correction), as in k2_tile.
+struct ZWin {
+    int lo;
+    float d0, step, inv;
+};
+__device__ __forceinline__ ZWin z_window(const DevGeom &g, const FxCol &cF, int m, int kfirst,
+                                         long long kfirst_fx) {
+    constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
+    const long long Z = cF.h0 + (long long)m * cF.h1;
+    const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;
+    ZWin zw;
+    zw.step = (float)(int)(Z >> 15) * kInv24;
+    zw.inv = __fdividef(1.f, zw.step);
+    const float zoff_f = g.cz - (float)(g.nv - 1) * 0.5f * zw.step;
+    int lo = (int)ceilf(((float)kfirst - zoff_f) * zw.inv - zw.inv);
+    const long long d_fx = 2LL * lo * Z + zoff - kfirst_fx;
+    float d0 = (float)(int)(d_fx >> 16) * kInv24;
+    if (d0 <= -1.f) {
+        ++lo;
+        d0 += zw.step;
+    } else if (d0 - zw.step > -1.f) {
+        --lo;
+        d0 -= zw.step;
+    }
+    zw.lo = lo;
+    zw.d0 = d0;
+    return zw;
+}
+
+// In-plane weight of voxel row bb from the crossing floor b0, fraction fb.
+__device__ __forceinline__ float inplane_weight(int b0, float fb, int bb) {
+    return (b0 == bb) ? 1.f - fb : ((b0 + 1 == bb) ? fb : 0.f);
+}
+
+// One warp's 2x2 group of voxel columns (i0 + x, j0 + y), x, y in {0, 1}: for
+// every view and every candidate detector column, the column's two planes of
+// the group (FAMY: planes j0, j0 + 1, in-plane i0, i0 + 1; else the other
+// way round) each give one z-profile, computed once and added to the two
+// voxel columns of that plane with their in-plane weights.  Every voxel gets
+// exactly the terms of k2_tile, in the same column order and the same
+// arithmetic, so the sums are bit-identical.
+template <int NTAP, int VPL, bool FAMY>
+__device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevGeom &g, const FxCol &cF,
+                                             const float *__restrict__ rcol, int i0, int j0, int kfirst,
+                                             long long kfirst_fx, int lo_max) {
+    const int mA = FAMY ? j0 : i0, bA = FAMY ? i0 : j0;
+    const int Na = FAMY ? g.ny : g.nx;
+    long long qb = cF.qb0 + (long long)mA * cF.qb1;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        if (p) qb += cF.qb1;
+        const int m = mA + p;
+        if (m >= Na) break;
+        const int b0 = fx_floor(qb);
+        const float fb = fx_frac(qb);
+        const float w0 = inplane_weight(b0, fb, bA), w1 = inplane_weight(b0, fb, bA + 1);
+        if (w0 == 0.f && w1 == 0.f) continue;
+        const ZWin zw = z_window(g, cF, m, kfirst, kfirst_fx);
+        float(&a0)[VPL] = acc[FAMY ? 0 : p][FAMY ? p : 0];
+        float(&a1)[VPL] = acc[FAMY ? 1 : p][FAMY ? p : 1];
+        const int nt = (int)(2.f * zw.inv * 1.0001f + 0.002f) + 1;
+        const bool inside = zw.lo >= -RT_PAD && zw.lo + (int)((float)VPL * zw.inv) + 2 <= lo_max;
+        if (__all_sync(0xffffffffu, inside))
+            column_taps2_nt<NTAP, VPL, false>(nt, a0, a1, w0, w1, rcol, zw.lo, zw.d0, zw.step, lo_max);
+        else
+            column_taps2_nt<NTAP, VPL, true>(nt, a0, a1, w0, w1, rcol, zw.lo, zw.d0, zw.step, lo_max);
+    }
+}
+
+// One block of 8 warps = 4 x 2 groups: voxel columns i in [8 gx, 8 gx + 8),
+// j in [4 gy, 4 gy + 4), z-span bz; the block's sum of squared gradient values
+// goes to *g2_partial (if not NULL).  Called by every thread.
+template <int NTAP, int VPL>
+__device__ __forceinline__ void k2_tile22(const BpArgs &a, int gx, int gy, int bz, double *g2_partial) {
+    const DevGeom &g = a.g;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int i0 = 8 * gx + 2 * (w & 3), j0 = 4 * gy + 2 * (w >> 2);
+    const int kfirst = bz * K2_LANES * VPL + VPL * lane;
+    float acc[2][2][VPL];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y)
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) acc[x][y][q] = 0.f;
+    const int rp = rt_pitch(g.nv);
+    const int nsel = (i0 < g.nx && j0 < g.ny) ? a.n_sel : 0;
+    const int lo_max = g.nv + RT_PAD - NTAP;
+    const long long kfirst_fx = (long long)kfirst << FX_BITS;
+    for (int s = 0; s < nsel; ++s) {
+        const int v = a.views[s];
+        const float2 cs = g.trig[v];
+        // the union of the four voxel columns' candidate windows (k2_tile's)
+        int iu_lo = g.nu, iu_hi = -1;
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int y = 0; y < 2; ++y) {
+                const float xc = ((float)(i0 + x) - g.cx) * g.vx;
+                const float yc = ((float)(j0 + y) - g.cy) * g.vy;
+                const float xi = xc * cs.x + yc * cs.y;
+                const float eta = -xc * cs.y + yc * cs.x;
+                const float iuc = eta * __fdividef(g.sdd, g.sod - xi) * g.inv_du + g.cu;
+                iu_lo = min(iu_lo, max(0, (int)ceilf(iuc - g.hwu)));
+                iu_hi = max(iu_hi, min(g.nu - 1, (int)floorf(iuc + g.hwu)));
+            }
+        for (int iu = iu_lo; iu <= iu_hi; ++iu) {
+            const size_t col = (size_t)v * g.nu + iu;
+            const FxCol cF = g.colF[col];
+            const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
+            if (g.colB[col].z != 0.f)
+                group_column<NTAP, VPL, true>(acc, g, cF, rcol, i0, j0, kfirst, kfirst_fx, lo_max);
+            else
+                group_column<NTAP, VPL, false>(acc, g, cF, rcol, i0, j0, kfirst, kfirst_fx, lo_max);
+        }
+    }
+    float g2 = 0.f;
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const int i = i0 + x, j = j0 + y;
+            if (i < g.nx && j < g.ny) {
+                float *out = a.gzi + ((size_t)j * g.nx + i) * g.nz;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int k = kfirst + q;
+                    if (k < g.nz) {
+                        const float val = a.scale * acc[x][y][q];
+                        out[k] = val;
+                        g2 = fmaf(val, val, g2);
+                    }
+                }
+            }
+        }
+    if (g2_partial) {
+        float vv[1] = {g2};
+        double o[1];
+        block_sum_f64<K2_LANES * K2_WARPS, 1>(vv, o);
+        if (threadIdx.x == 0 && threadIdx.y == 0) *g2_partial = o[0];
+    }
 }
 
 // One block's work: voxel columns i = bx*8 .. bx*8+7 of row j, z-span bz;
@@ -199,6 +391,12 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) k2_backproject(const Bp
     k2_tile<NTAP, K2_VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
 }
 
+template <int NTAP, int VPL>
+__global__ void __launch_bounds__(K2_LANES *K2_WARPS, 4) k2_backproject22(const BpArgs a) {
+    const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    k2_tile22<NTAP, VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
+}
+
 // Persistent batched backprojector: the blocks of k2_backproject of every
 // volume, taken from an atomic counter.  Each volume keeps its own voxels per
 // lane (its geometry's k2_vpl, a warp-uniform switch).  Registers are capped
@@ -258,13 +456,25 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const Ba
 }  // namespace
 
 
-int backproject_num_partials(const DevGeom &g) {
+static dim3 k2_grid(const DevGeom &g) {
     const int vpl = k2_vpl_of(g);
-    return ((g.nx + K2_WARPS - 1) / K2_WARPS) * g.ny * ((g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
+    const unsigned gz = (g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl);
+    if (k2_group_of(g)) return dim3((g.nx + 7) / 8, (g.ny + 3) / 4, gz);
+    return dim3((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, gz);
+}
+
+int backproject_num_partials(const DevGeom &g) {
+    const dim3 gr = k2_grid(g);
+    return (int)(gr.x * gr.y * gr.z);
 }
 
 template <int NT>
 static void launch_k2(int vpl, dim3 grid, dim3 block, cudaStream_t st, const BpArgs &a) {
+    if (k2_group_of(a.g)) {
+        if (vpl == 8) k2_backproject22<NT, 8><<<grid, block, 0, st>>>(a);
+        else k2_backproject22<NT, 4><<<grid, block, 0, st>>>(a);
+        return;
+    }
     switch (vpl) {
         case 2: k2_backproject<NT, 2><<<grid, block, 0, st>>>(a); break;
         case 8: k2_backproject<NT, 8><<<grid, block, 0, st>>>(a); break;
@@ -317,7 +527,7 @@ cudaError_t launch_backproject(const DevGeom &g, const float *rt, const int32_t 
     a.gzi = gzi;
     dim3 block(K2_LANES, K2_WARPS);
     const int vpl = k2_vpl_of(g);
-    dim3 grid((g.nx + K2_WARPS - 1) / K2_WARPS, g.ny, (g.nz + K2_LANES * vpl - 1) / (K2_LANES * vpl));
+    const dim3 grid = k2_grid(g);
     switch (g.ntap) {  // rows per voxel and column, fixed per geometry (<= RT_PAD)
         case 1: launch_k2<1>(vpl, grid, block, st, a); break;
         case 2: launch_k2<2>(vpl, grid, block, st, a); break;

@@ -67,7 +67,7 @@ def _singles(fbl, Gs, bs, iters, dtype, torch_dtype, proposal=None, **extra):
     return xs, traces
 
 
-@pytest.mark.parametrize("cfg", [(8, 1, 4), (4, 0, 8), MIXED])
+@pytest.mark.parametrize("cfg", [(8, 1, 4), (4, 0, 8), MIXED, [(8, 1, 24), (8, 0, 28), (8, 1, 8), (8, 0, 24)]])
 def test_batch_is_bit_identical_to_single_volume_solvers(data, cfg):
     import torch
     import paper_2605_12085_gb300 as fbl
