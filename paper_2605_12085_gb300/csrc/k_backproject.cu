@@ -161,10 +161,10 @@ struct ZWin {
     int lo;
     float d0, step, inv;
 };
-__device__ __forceinline__ ZWin z_window(const DevGeom &g, const FxCol &cF, int m, int kfirst,
-                                         long long kfirst_fx) {
+__device__ __forceinline__ ZWin z_window(const DevGeom &g, const FxCol *cF, int m, int kfirst) {
     constexpr float kInv24 = 1.0f / 16777216.0f;  // 2^-24 (Q.40 >> 16)
-    const long long Z = cF.h0 + (long long)m * cF.h1;
+    const long long kfirst_fx = (long long)kfirst << FX_BITS;
+    const long long Z = __ldg(&cF->h0) + (long long)m * __ldg(&cF->h1);
     const long long zoff = g.cz_fx - (long long)(g.nv - 1) * Z;
     ZWin zw;
     zw.step = (float)(int)(Z >> 15) * kInv24;
@@ -198,22 +198,23 @@ __device__ __forceinline__ float inplane_weight(int b0, float fb, int bb) {
 // exactly the terms of k2_tile, in the same column order and the same
 // arithmetic, so the sums are bit-identical.
 template <int NTAP, int VPL, bool FAMY>
-__device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevGeom &g, const FxCol &cF,
+__device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevGeom &g, const FxCol *cF,
                                              const float *__restrict__ rcol, int i0, int j0, int kfirst,
-                                             long long kfirst_fx, int lo_max) {
+                                             int lo_max) {
     const int mA = FAMY ? j0 : i0, bA = FAMY ? i0 : j0;
     const int Na = FAMY ? g.ny : g.nx;
-    long long qb = cF.qb0 + (long long)mA * cF.qb1;
+    // the column constants are read where they are used (an L1 broadcast) rather than kept live
+    long long qb = __ldg(&cF->qb0) + (long long)mA * __ldg(&cF->qb1);
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        if (p) qb += cF.qb1;
+        if (p) qb += __ldg(&cF->qb1);
         const int m = mA + p;
         if (m >= Na) break;
         const int b0 = fx_floor(qb);
         const float fb = fx_frac(qb);
         const float w0 = inplane_weight(b0, fb, bA), w1 = inplane_weight(b0, fb, bA + 1);
         if (w0 == 0.f && w1 == 0.f) continue;
-        const ZWin zw = z_window(g, cF, m, kfirst, kfirst_fx);
+        const ZWin zw = z_window(g, cF, m, kfirst);
         float(&a0)[VPL] = acc[FAMY ? 0 : p][FAMY ? p : 0];
         float(&a1)[VPL] = acc[FAMY ? 1 : p][FAMY ? p : 1];
         const int nt = (int)(2.f * zw.inv * 1.0001f + 0.002f) + 1;
@@ -244,7 +245,6 @@ __device__ __forceinline__ void k2_tile22(const BpArgs &a, int gx, int gy, int b
     const int rp = rt_pitch(g.nv);
     const int nsel = (i0 < g.nx && j0 < g.ny) ? a.n_sel : 0;
     const int lo_max = g.nv + RT_PAD - NTAP;
-    const long long kfirst_fx = (long long)kfirst << FX_BITS;
     for (int s = 0; s < nsel; ++s) {
         const int v = a.views[s];
         const float2 cs = g.trig[v];
@@ -264,12 +264,12 @@ __device__ __forceinline__ void k2_tile22(const BpArgs &a, int gx, int gy, int b
             }
         for (int iu = iu_lo; iu <= iu_hi; ++iu) {
             const size_t col = (size_t)v * g.nu + iu;
-            const FxCol cF = g.colF[col];
+            const FxCol *cF = g.colF + col;
             const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
             if (g.colB[col].z != 0.f)
-                group_column<NTAP, VPL, true>(acc, g, cF, rcol, i0, j0, kfirst, kfirst_fx, lo_max);
+                group_column<NTAP, VPL, true>(acc, g, cF, rcol, i0, j0, kfirst, lo_max);
             else
-                group_column<NTAP, VPL, false>(acc, g, cF, rcol, i0, j0, kfirst, kfirst_fx, lo_max);
+                group_column<NTAP, VPL, false>(acc, g, cF, rcol, i0, j0, kfirst, lo_max);
         }
     }
     float g2 = 0.f;

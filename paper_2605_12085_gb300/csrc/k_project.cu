@@ -114,7 +114,7 @@ constexpr int K1_CHUNK = 32;
 // lies outside the ray's own interval, j outside [r0, r1], reads the zero row
 // k = -1 with weight 0.  Samples with j even go to s0, odd to s1, each in
 // plane order.
-template <bool MASKED, typename TX>
+template <bool MASKED, bool PIPE, typename TX>
 __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int2 *__restrict__ tab, int len,
                                            int bs, long long &qz, long long qz1, int r0, int r1, float &s0,
                                            float &s1) {
@@ -136,13 +136,64 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
         const float hi = fmaf(fb, v11 - v10, v10);
         return fmaf(fz, hi - lo, lo);
     };
+    if (!PIPE) {
+        int j = 0;
+#pragma unroll 1
+        for (; j + 1 < len; j += 2) {
+            s0 += sample(j);
+            s1 += sample(j + 1);
+        }
+        if (j < len) s0 += sample(j);
+        return;
+    }
+    // PIPE: the next sample's loads are issued before the current sample is
+    // interpolated (same operations, same order per partial sum).  Measured
+    // faster for the store-mode projector (720 views at 512^3: 103.8 against
+    // 117.5 ms) and slower in the residual and objective modes (8.5 against
+    // 6.5 ms per 40-view launch), which keep the plain loop.
+    struct Smp {
+        float v00, v10, v01, v11, fb, fz;
+    };
+    auto fetch = [&](int j, Smp &o) {
+        const int2 e = tab[j];
+        int k0 = fx32_floor(qz);
+        float fz = fx32_frac(qz);
+        if (MASKED) {
+            const bool in = (unsigned)(j - r0) <= (unsigned)(r1 - r0);
+            k0 = in ? k0 : -1;
+            fz = in ? fz : 0.f;
+        }
+        qz += qz1;
+        const TX *p = vol + (e.x + k0);
+        o.fb = __int_as_float(e.y);
+        o.fz = fz;
+        o.v00 = ldg_f32(p);
+        o.v10 = ldg_f32(p + 1);
+        o.v01 = ldg_f32(p + bs);
+        o.v11 = ldg_f32(p + bs + 1);
+    };
+    auto value = [](const Smp &o) {
+        const float lo = fmaf(o.fb, o.v01 - o.v00, o.v00);
+        const float hi = fmaf(o.fb, o.v11 - o.v10, o.v10);
+        return fmaf(o.fz, hi - lo, lo);
+    };
+    Smp a, b;
+    fetch(0, a);
     int j = 0;
 #pragma unroll 1
-    for (; j + 1 < len; j += 2) {
-        s0 += sample(j);
-        s1 += sample(j + 1);
+    for (; j + 2 < len; j += 2) {
+        fetch(j + 1, b);
+        s0 += value(a);
+        fetch(j + 2, a);
+        s1 += value(b);
     }
-    if (j < len) s0 += sample(j);
+    if (j + 1 < len) {
+        fetch(j + 1, b);
+        s0 += value(a);
+        s1 += value(b);
+    } else {
+        s0 += value(a);
+    }
 }
 
 // The Q.32 line a ray's samples follow from the warp's first plane u0:
@@ -258,10 +309,11 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
                     tab[lane] = make_int2(base + m * ps + fx_floor(qb) * bs, __float_as_int(fx_frac(qb)));
                 }
                 __syncwarp();
+                constexpr bool PIPE = MODE == PROJ_STORE;
                 if (SPLIT && mb >= c0 && mb + len - 1 <= c1)
-                    chunk_loop<false, TX>(vol, tab, len, bs, qz, qz1, 0, 0, s0, s1);
+                    chunk_loop<false, PIPE, TX>(vol, tab, len, bs, qz, qz1, 0, 0, s0, s1);
                 else
-                    chunk_loop<true, TX>(vol, tab, len, bs, qz, qz1, o0 - mb, o1 - mb, s0, s1);
+                    chunk_loop<true, PIPE, TX>(vol, tab, len, bs, qz, qz1, o0 - mb, o1 - mb, s0, s1);
                 __syncwarp();
             }
             acc = s0 + s1;
