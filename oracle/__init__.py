@@ -13,12 +13,17 @@ Contents:
   * ``fdk`` -- the FDK reconstruction (cosine weighting, Ram-Lak filter,
     weighted backprojection) in numpy float64;
   * ``tv`` -- other regularisers: the box-constrained l1 prox and the
-    isotropic TV prox by FGP iterations on the dual, in numpy float64.
+    isotropic TV prox by FGP iterations on the dual, in numpy float64;
+  * ``mlp`` -- the step-proposal network (forward, gradient, Adam) in FP64;
+  * ``proposal`` -- the learned step proposal inside Algorithm 1 (features,
+    network output, first grid index) driving ``fblisa.fb_step``.
 
 Pins (checks against facts the paper and mathematics fix, not against this
-code) live in ``tests/test_oracle_*.py``.  One function is "parity unpinned"
-against the paper itself: the whole FB-LISA trajectory on the paper's walnut
-data (the data are not available); it is pinned only through its parts.
+code) live in ``tests/test_oracle_*.py``.  Parity unpinned against the paper
+itself: the whole FB-LISA trajectory on the paper's walnut data (the data are
+not available), pinned only through its parts, and the learned proposal, which
+has no counterpart in the paper (pinned by the properties listed in
+``proposal.py``).
 """
 from __future__ import annotations
 
