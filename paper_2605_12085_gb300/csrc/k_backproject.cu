@@ -57,6 +57,23 @@ struct BpArgs {
     double *g2_partials;  // optional: per-block sum of the squared gradient
 };
 
+// Drop the rows that fell below the next voxel's footprint: while d0 <= -1,
+// one row up (lo and r advance together; the caller uses one of them).  A
+// column reached by at most NT rows per voxel has rows spaced step > 2/NT
+// apart, so a voxel drops at most (NT + 1) / 2 rows: that many predicated
+// steps, no data-dependent loop, so the compiler can overlap the taps of
+// consecutive voxels.  The same additions as the loop, in the same order.
+template <int NT>
+__device__ __forceinline__ void advance_window(float &d0, float step, int &lo, const float *&r) {
+#pragma unroll
+    for (int c = 0; c < (NT + 1) / 2; ++c) {
+        const bool p = d0 <= -1.f;
+        d0 = p ? d0 + step : d0;
+        lo += p ? 1 : 0;
+        r += p ? 1 : 0;
+    }
+}
+
 // The taps of one candidate column for the lane's VPL voxels: window of NT
 // rows from `lo`, whose first crossing lies d0 voxels from the lane's first
 // voxel (-1 < d0 <= -1 + step).  After each voxel the window drops the rows
@@ -79,11 +96,7 @@ __device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const f
         acc[q] = fmaf(wb, sz, acc[q]);
         // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
         d0 -= 1.f;
-        while (d0 <= -1.f) {
-            if (CLAMP) ++lo;
-            else ++r;
-            d0 += step;
-        }
+        advance_window<NT>(d0, step, lo, r);
     }
 }
 
@@ -135,11 +148,7 @@ __device__ __forceinline__ void column_taps2(float (&accA)[VPL], float (&accB)[V
         accA[q] = fmaf(wA, sz, accA[q]);
         accB[q] = fmaf(wB, sz, accB[q]);
         d0 -= 1.f;
-        while (d0 <= -1.f) {
-            if (CLAMP) ++lo;
-            else ++r;
-            d0 += step;
-        }
+        advance_window<NT>(d0, step, lo, r);
     }
 }
 
