@@ -194,7 +194,7 @@ FBL_API fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n
  * voxels per lane in each (a detector column's z-profile in a plane is then
  * formed once for its two in-plane neighbours; the sums are the same);
  * FBL_E_INVAL otherwise.  The batched solver runs k1_split 2 volumes with the
- * unmasked-middle loop and 2x2 group volumes with one voxel column per warp. */
+ * unmasked-middle loop. */
 FBL_API fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                        int32_t k2_vpl);
 

@@ -2180,9 +2180,6 @@ extern "C" fbl_status fblisa_batch_create(const fbl_geometry *const *geoms, cons
         p.use_graph = 0;
         fbl_solver *s = nullptr;
         st = fblisa_create(geoms[v], &p, &s);
-        // the batched backprojector takes one voxel column per warp: a 2x2 group
-        // configuration runs with its voxels per lane (the same sums)
-        if (!st && (s->dg.k2_vpl == 24 || s->dg.k2_vpl == 28)) s->dg.k2_vpl -= 20;
         if (st) {
             std::string keep = g_last_error;
             batch_free(bt);

@@ -406,12 +406,13 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 4) k2_backproject22(const 
     k2_tile22<NTAP, VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
 }
 
-// Persistent batched backprojector: the blocks of k2_backproject of every
-// volume, taken from an atomic counter.  Each volume keeps its own voxels per
-// lane (its geometry's k2_vpl, a warp-uniform switch).  Registers are capped
-// at 48 (5 blocks per SM), as for the batched projector.
+// Persistent batched backprojector: the blocks of k2_backproject (or of the
+// 2x2 group kernel) of every volume, taken from an atomic counter.  Each volume
+// keeps its own launch configuration (its geometry's k2_vpl, a warp-uniform
+// switch).  Registers are capped at 64 (4 blocks per SM), what the group tiles
+// need.
 template <int NTAP>
-__global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const BatchHdr *hdr,
+__global__ void __launch_bounds__(K2_LANES *K2_WARPS, 4) kb_backproject(const BatchHdr *hdr,
                                                                         const BatchVol *vols, int *ctr) {
     __shared__ int s_tile;
     __shared__ BpArgs sa;
@@ -439,6 +440,15 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) kb_backproject(const Ba
         const BpArgs &a = sa;
         const int local = t - bv.first[1];
         const int vpl = k2_vpl_of(bv.g);
+        double *gpart = bv.partials + local;
+        if (k2_group_of(bv.g)) {
+            const int gxn = (bv.g.nx + 7) / 8, gyn = (bv.g.ny + 3) / 4;
+            const int gx = local % gxn;
+            const int rest = local / gxn;
+            if (vpl == 8) k2_tile22<NTAP, 8>(a, gx, rest % gyn, rest / gyn, gpart);
+            else k2_tile22<NTAP, 4>(a, gx, rest % gyn, rest / gyn, gpart);
+            continue;
+        }
         const int gx = (bv.g.nx + K2_WARPS - 1) / K2_WARPS;
         const int bx = local % gx;
         const int rest = local / gx;
