@@ -169,7 +169,7 @@ FBL_API void geometry_destroy(fbl_geometry *g);
 
 /* Launch configurations tried by the autotuner and their measured times. */
 typedef struct {
-    float k1_ms[5];     /* projector, (cols, split) = (8,1), (8,0), (4,1), (4,0), (8,2) */
+    float k1_ms[5];     /* projector, (cols, k1_split) = (8,1), (8,0), (4,1), (4,0), (8,2) */
     float k2_ms[6];     /* backprojector, k2_vpl = 4, 2, 8, 16, 24, 28 (geometry_set_launch) */
     int32_t k1_cols, k1_split, k2_vpl;  /* the chosen configuration */
 } fbl_tune_report;
@@ -185,8 +185,9 @@ FBL_API fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n
                                      fbl_tune_report *report);
 
 /* Set the launch configuration by hand: k1_cols in {4, 8}; k1_split = the
- * projector's plane loop: 0 masked, 1 with an unmasked middle phase, 2 the
- * volume staged through shared memory by TMA brick copies (8 columns per
+ * projector's plane loop: 0 plain, 1 with each sample's loads issued one
+ * sample ahead in the residual and objective modes (the store mode always
+ * does), 2 the volume staged through shared memory by TMA brick copies (8 columns per
  * block whatever k1_cols; its bounded waits report FBL_E_TIMEOUT from the next
  * synchronous call on the geometry, the results stay correct); k2_vpl = the
  * backprojector's work per warp: 2, 4, 8 or 16 consecutive voxels per lane of
@@ -194,7 +195,7 @@ FBL_API fbl_status geometry_autotune(fbl_geometry *g, int32_t x_dtype, int32_t n
  * voxels per lane in each (a detector column's z-profile in a plane is then
  * formed once for its two in-plane neighbours; the sums are the same);
  * FBL_E_INVAL otherwise.  The batched solver runs k1_split 2 volumes with the
- * unmasked-middle loop. */
+ * loads-ahead loop. */
 FBL_API fbl_status geometry_set_launch(fbl_geometry *g, int32_t k1_cols, int32_t k1_split,
                                        int32_t k2_vpl);
 

@@ -42,8 +42,10 @@ template <typename T> __device__ __forceinline__ float ldg_f32(const T *p) { ret
 // in-plane strides swapped.  The detector rows of one column (a warp of K1)
 // sample consecutive k.  A bilinear footprint with -1 < q_b < Nb and
 // -1 < q_z < nz reads in bounds and sees the zero boundary without a branch.
-// PL = 16 bytes of elements keeps each row's interior 16-byte aligned; pitch
-// is a multiple of PL with at least one zero after the last element.
+// PL = 16 bytes of elements (at least 2) keeps each row's interior 16-byte
+// aligned; pitch is a multiple of PL with at least two zeros after the last
+// element, so a bilinear footprint whose z row is clamped to [-2, nz] reads
+// only zeros outside the volume.
 // The gradient uses the unpadded z-innermost order [j][i][k].
 // ---------------------------------------------------------------------------
 struct ZLayout {
@@ -65,7 +67,7 @@ inline ZLayout make_layout(int nx, int ny, int nz, int esize) {
     L.ny = ny;
     L.nz = nz;
     L.PL = 16 / esize;
-    const int need = L.PL + nz + 1;
+    const int need = L.PL + nz + 2;
     L.pitch = (need + L.PL - 1) / L.PL * L.PL;
     return L;
 }
@@ -129,7 +131,7 @@ struct DevGeom {
     int ntap;                    // detector rows that can touch one voxel in one column
     // launch configuration (chosen by the autotuner; defaults 8 / 1 / 4)
     int k1_cols;                 // projector: detector columns per block (4 or 8)
-    int k1_split;                // projector plane loop: 0 masked, 1 unmasked middle phase, 2 TMA-staged bricks
+    int k1_split;                // projector plane loop: 0 plain, 1 loads one sample ahead, 2 TMA-staged bricks
     int k2_vpl;                  // backprojector: consecutive voxels per lane (2, 4, 8 or 16)
     long long cz_fx;             // cz in Q.40
     const float4 *colA;          // [n_views][nu] (qb0, qb1, zc0, zc1) in FP32, for range estimates

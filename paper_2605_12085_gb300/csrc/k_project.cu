@@ -110,63 +110,27 @@ constexpr int K1_CHUNK = 32;
 // The samples j = 0 .. len-1 of one table chunk for a lane's ray.  tab[j] =
 // (element offset of plane mb + j at in-plane row b0, in-plane fraction fb),
 // shared by the warp's rays (one detector column); qz is the lane's vertical
-// crossing at plane mb in Q.32 (advanced to mb + len).  MASKED: a sample whose plane
-// lies outside the ray's own interval, j outside [r0, r1], reads the zero row
-// k = -1 with weight 0.  Samples with j even go to s0, odd to s1, each in
-// plane order.
-template <bool MASKED, bool PIPE, typename TX>
+// crossing at plane mb in Q.32 (advanced to mb + len).  The warp walks the
+// union of its rays' intervals, and the in-plane crossing is common to the
+// column, so a sample outside its own ray's interval lies below or above the
+// volume in z: its row k0 is clamped to [-2, nz], where both taps read the two
+// zero elements each z-row carries at either end, and it adds exactly +0 --
+// no mask.  Samples with j even go to s0, odd to s1, each in plane order.
+// PIPE: the next sample's loads are issued before the current sample is
+// interpolated (same operations, same order per partial sum).
+template <bool PIPE, typename TX>
 __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int2 *__restrict__ tab, int len,
-                                           int bs, long long &qz, long long qz1, int r0, int r1, float &s0,
-                                           float &s1) {
-    auto sample = [&](int j) {
-        const int2 e = tab[j];
-        int k0 = fx32_floor(qz);
-        float fz = fx32_frac(qz);
-        if (MASKED) {
-            const bool in = (unsigned)(j - r0) <= (unsigned)(r1 - r0);
-            k0 = in ? k0 : -1;
-            fz = in ? fz : 0.f;
-        }
-        qz += qz1;
-        const TX *p = vol + (e.x + k0);
-        const float fb = __int_as_float(e.y);
-        const float v00 = ldg_f32(p), v10 = ldg_f32(p + 1);
-        const float v01 = ldg_f32(p + bs), v11 = ldg_f32(p + bs + 1);
-        const float lo = fmaf(fb, v01 - v00, v00);
-        const float hi = fmaf(fb, v11 - v10, v10);
-        return fmaf(fz, hi - lo, lo);
-    };
-    if (!PIPE) {
-        int j = 0;
-#pragma unroll 1
-        for (; j + 1 < len; j += 2) {
-            s0 += sample(j);
-            s1 += sample(j + 1);
-        }
-        if (j < len) s0 += sample(j);
-        return;
-    }
-    // PIPE: the next sample's loads are issued before the current sample is
-    // interpolated (same operations, same order per partial sum).  Measured
-    // faster for the store-mode projector (720 views at 512^3: 103.8 against
-    // 117.5 ms) and slower in the residual and objective modes (8.5 against
-    // 6.5 ms per 40-view launch), which keep the plain loop.
+                                           int bs, int nz, long long &qz, long long qz1, float &s0, float &s1) {
     struct Smp {
         float v00, v10, v01, v11, fb, fz;
     };
     auto fetch = [&](int j, Smp &o) {
         const int2 e = tab[j];
-        int k0 = fx32_floor(qz);
-        float fz = fx32_frac(qz);
-        if (MASKED) {
-            const bool in = (unsigned)(j - r0) <= (unsigned)(r1 - r0);
-            k0 = in ? k0 : -1;
-            fz = in ? fz : 0.f;
-        }
+        const int k0 = min(max(fx32_floor(qz), -2), nz);
+        o.fz = fx32_frac(qz);
         qz += qz1;
         const TX *p = vol + (e.x + k0);
         o.fb = __int_as_float(e.y);
-        o.fz = fz;
         o.v00 = ldg_f32(p);
         o.v10 = ldg_f32(p + 1);
         o.v01 = ldg_f32(p + bs);
@@ -177,6 +141,23 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
         const float hi = fmaf(o.fb, o.v11 - o.v10, o.v10);
         return fmaf(o.fz, hi - lo, lo);
     };
+    if (!PIPE) {
+        int j = 0;
+#pragma unroll 1
+        for (; j + 1 < len; j += 2) {
+            Smp a, b;
+            fetch(j, a);
+            fetch(j + 1, b);
+            s0 += value(a);
+            s1 += value(b);
+        }
+        if (j < len) {
+            Smp a;
+            fetch(j, a);
+            s0 += value(a);
+        }
+        return;
+    }
     Smp a, b;
     fetch(0, a);
     int j = 0;
@@ -251,9 +232,9 @@ __device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, in
 // the in-plane crossing q_b is common to the column's rays, so its floor
 // (folded with the plane into an element offset) and fraction are computed
 // once per plane for the whole warp and read back by every sample with one
-// broadcast shared-memory load.  SPLIT: chunks inside the common part [c0, c1]
-// of the intervals run without per-sample masks.
-template <typename TX, typename TB, typename TO, int MODE, int COLS, bool SPLIT>
+// broadcast shared-memory load.  PIPE: the residual and objective modes issue
+// each sample's loads one sample ahead (launch configuration k1_split = 1).
+template <typename TX, typename TB, typename TO, int MODE, int COLS, bool PIPE>
 __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int band, double *partial) {
     __shared__ int2 tab_all[COLS][K1_CHUNK];
     const DevGeom &g = a.g;
@@ -276,16 +257,14 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
         if (iv < g.nv) plane_range(rc, Na, m0, m1);
         constexpr int BIG = 1 << 30;
         const bool has = m0 <= m1;
-        // a ray with no sample is pinned to the zero row k = -1 with weight 0
+        // a ray with no sample is pinned below the volume (reads the zero elements)
         if (!has) {
-            rc.qz0 = -(1LL << FX_BITS);
+            rc.qz0 = -(2LL << FX_BITS);
             rc.qz1 = 0;
         }
-        // warp union of the intervals, and their common part (rays without samples excluded)
+        // warp union of the intervals (rays without samples excluded)
         const int u0 = __reduce_min_sync(0xffffffffu, has ? m0 : BIG);
         const int u1 = __reduce_max_sync(0xffffffffu, has ? m1 : -1);
-        const int c0 = __reduce_max_sync(0xffffffffu, has ? m0 : -BIG);
-        const int c1 = __reduce_min_sync(0xffffffffu, has ? m1 : BIG);
         float acc = 0.f;
         if (u0 <= u1) {
             const TX *vol = (const TX *)a.vol;
@@ -295,8 +274,6 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
             // element (b, m, k) = vol + [PL + (m+1)*ps + (b+1)*bs + k]
             const int base = L.PL + ps + bs;
             int2 *tab = tab_all[threadIdx.y];
-            // the ray's own interval (a ray without samples reads zeros anyway)
-            const int o0 = has ? m0 : u0, o1 = has ? m1 : u1;
             // the vertical crossing in Q.32 from the warp's first plane (ray_z32)
             long long qz, qz1;
             ray_z32(rc, u0, qz, qz1);
@@ -309,11 +286,9 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
                     tab[lane] = make_int2(base + m * ps + fx_floor(qb) * bs, __float_as_int(fx_frac(qb)));
                 }
                 __syncwarp();
-                constexpr bool PIPE = MODE == PROJ_STORE;
-                if (SPLIT && mb >= c0 && mb + len - 1 <= c1)
-                    chunk_loop<false, PIPE, TX>(vol, tab, len, bs, qz, qz1, 0, 0, s0, s1);
-                else
-                    chunk_loop<true, PIPE, TX>(vol, tab, len, bs, qz, qz1, o0 - mb, o1 - mb, s0, s1);
+                // the store mode always issues loads one sample ahead; the residual
+                // and objective modes when the launch configuration asks (PIPE)
+                chunk_loop<MODE == PROJ_STORE || PIPE, TX>(vol, tab, len, bs, g.nz, qz, qz1, s0, s1);
                 __syncwarp();
             }
             acc = s0 + s1;
@@ -336,10 +311,10 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
 // and the extra resident warps hide more of that latency than the capped
 // allocation costs (measured 7.09 against 7.68 ms per 40-view launch at 512^3;
 // a 32-register cap is slower).
-template <typename TX, typename TB, typename TO, int MODE, int COLS, bool SPLIT>
+template <typename TX, typename TB, typename TO, int MODE, int COLS, bool PIPE>
 __global__ void __launch_bounds__(32 * COLS, 48 / COLS) k1_project(const ProjArgs a) {
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    k1_tile<TX, TB, TO, MODE, COLS, SPLIT>(a, blockIdx.x, blockIdx.y, blockIdx.z,
+    k1_tile<TX, TB, TO, MODE, COLS, PIPE>(a, blockIdx.x, blockIdx.y, blockIdx.z,
                                            MODE != PROJ_STORE ? a.partials + blk : nullptr);
 }
 
@@ -461,7 +436,7 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
         s_famY = f;
     }
     __syncthreads();
-    if (s_mixed) {  // the masked loop: the same sums as the brick path
+    if (s_mixed) {  // the plain loop: the same sums as the brick path
         k1_tile<TX, TB, TO, MODE, TMA_COLS, false>(a, cb, s, band, partial);
         return;
     }
@@ -522,10 +497,10 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
     __syncthreads();
     const int U0 = s_U0, U1 = s_U1;
     const int nch = U1 >= U0 ? (U1 - U0 + P) / P : 0;
-    const int o0 = has ? m0 : BIG, o1 = has ? m1 : -1;
-    // the lane's vertical crossing on k1_tile's Q.32 line from the warp's first plane
-    long long qz32_u0 = 0, qz1_32 = 0;
-    if (u0 <= u1) ray_z32(rc, u0, qz32_u0, qz1_32);
+    // the lane's vertical crossing on k1_tile's Q.32 line from the warp's first
+    // plane; a ray without samples is pinned below the volume, as in k1_tile
+    long long qz32_u0 = -(2LL << 32), qz1_32 = 0;
+    if (has && u0 <= u1) ray_z32(rc, u0, qz32_u0, qz1_32);
 
     // produce chunk c into buffer c & 1 (one warp; lanes 0..7 take a column each)
     auto produce = [&](int c) {
@@ -602,29 +577,27 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
         for (int m = pa; m <= pb; ++m) {
             const int b0 = fx_floor(qb);
             const float fb = fx_frac(qb);
-            const int k0 = fx32_floor(qz);
+            // k1_tile's clamp: outside its ray's interval a sample reads zero elements
+            const int k0 = min(max(fx32_floor(qz), -2), g.nz);
             const float fz = fx32_frac(qz);
-            float val = 0.f;
-            if (m >= o0 && m <= o1) {
-                float v00, v10, v01, v11;
-                const int kk = k0 - mt.klo, bb = b0 - mt.blo, mm = m - mt.mc;
-                if (ok && (unsigned)kk <= (unsigned)(KZ - 2) && (unsigned)bb <= (unsigned)(KB - 2)) {
-                    const int idx = (famY ? (mm * KB + bb) * KZ : (bb * P + mm) * KZ) + kk;
-                    v00 = to_f32(br[idx]);
-                    v10 = to_f32(br[idx + 1]);
-                    v01 = to_f32(br[idx + bstride]);
-                    v11 = to_f32(br[idx + bstride + 1]);
-                } else {
-                    const TX *p = vol + (base + m * ps + b0 * bs + k0);
-                    v00 = ldg_f32(p);
-                    v10 = ldg_f32(p + 1);
-                    v01 = ldg_f32(p + bs);
-                    v11 = ldg_f32(p + bs + 1);
-                }
-                const float lo = fmaf(fb, v01 - v00, v00);
-                const float hi = fmaf(fb, v11 - v10, v10);
-                val = fmaf(fz, hi - lo, lo);
+            float v00, v10, v01, v11;
+            const int kk = k0 - mt.klo, bb = b0 - mt.blo, mm = m - mt.mc;
+            if (ok && (unsigned)kk <= (unsigned)(KZ - 2) && (unsigned)bb <= (unsigned)(KB - 2)) {
+                const int idx = (famY ? (mm * KB + bb) * KZ : (bb * P + mm) * KZ) + kk;
+                v00 = to_f32(br[idx]);
+                v10 = to_f32(br[idx + 1]);
+                v01 = to_f32(br[idx + bstride]);
+                v11 = to_f32(br[idx + bstride + 1]);
+            } else {
+                const TX *p = vol + (base + m * ps + b0 * bs + k0);
+                v00 = ldg_f32(p);
+                v10 = ldg_f32(p + 1);
+                v01 = ldg_f32(p + bs);
+                v11 = ldg_f32(p + bs + 1);
             }
+            const float lo = fmaf(fb, v01 - v00, v00);
+            const float hi = fmaf(fb, v11 - v10, v10);
+            const float val = fmaf(fz, hi - lo, lo);
             // the same partition of the sum as k1_tile: by the parity of m - u0
             if ((m - u0) & 1) s1 += val; else s0 += val;
             qb += rc.qb1;
