@@ -21,15 +21,16 @@
 // planes at a time, into a shared-memory table (plane and row folded into one
 // element offset, and the fraction) that every sample reads with one
 // broadcast load; a sample then costs one 64-bit add and a funnel shift for
-// its vertical crossing, four loads and three interpolations.  Each ray's plane interval
-// [m0, m1] is the exact set of planes whose crossing lies inside
-// (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp walks
-// the union of its rays' intervals -- without per-sample masks where they all
-// overlap, and with masks at the two ends, where a ray outside its own
-// interval samples the zero row k = -1 with weight 0.  Interpolation and the ray sum
-// are FP32 (two partial sums, by the parity of the plane index counted from
-// the warp's first plane); the squared residuals are summed in FP64 across
-// threads and blocks in a fixed order.
+// its vertical crossing, a clamp, four loads and three interpolations.  Each
+// ray's plane interval [m0, m1] is the exact set of planes whose crossing lies
+// inside (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp
+// walks the union of its rays' intervals with no per-sample mask: the
+// in-plane crossing is common to the warp, so a ray outside its own interval
+// is below or above the volume in z, and its clamped row reads the zero
+// elements at the ends of the z rows.  Interpolation and the ray sum are FP32
+// (two partial sums, by the parity of the plane index counted from the warp's
+// first plane); the squared residuals are summed in FP64 across threads and
+// blocks in a fixed order.
 #include <algorithm>
 #include <climits>
 
