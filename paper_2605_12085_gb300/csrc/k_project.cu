@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
 // outside the plane loop cost less than the occupancy a 64-register
 // allocation loses (16-volume workload: 96.4 against 102.9 ms per iteration).
 template <typename TX, typename TB, int MODE, int COLS>
-__global__ void __launch_bounds__(32 * COLS, 40 / COLS) kb_project(const BatchHdr *hdr, const BatchVol *vols,
+__global__ void __launch_bounds__(32 * COLS, 48 / COLS) kb_project(const BatchHdr *hdr, const BatchVol *vols,
                                                                    int *ctr) {
     __shared__ int s_tile;
     __shared__ ProjArgs sa;
