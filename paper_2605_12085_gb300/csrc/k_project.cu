@@ -624,9 +624,9 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
 // Persistent batched projector: tiles of all volumes (the blocks of
 // k1_project, volume by volume) taken from an atomic counter.  MODE NORM
 // covers only this trial round's searching volumes.  Registers are capped at
-// the single-volume kernel's 48 (40 warps per SM): the few bytes this spills
-// outside the plane loop cost less than the occupancy a 64-register
-// allocation loses (16-volume workload: 96.4 against 102.9 ms per iteration).
+// the single-volume kernel's 40 (48 warps per SM): the few bytes this spills
+// outside the plane loop cost less than the occupancy a 48-register allocation
+// loses (16-volume workload 96^3..320^3: 84.7 against 86.6 ms per iteration).
 template <typename TX, typename TB, int MODE, int COLS>
 __global__ void __launch_bounds__(32 * COLS, 48 / COLS) kb_project(const BatchHdr *hdr, const BatchVol *vols,
                                                                    int *ctr) {
