@@ -9,24 +9,25 @@
 //
 // Work decomposition.  A warp owns 32*VPL voxels of one (i, j) column along z
 // (lane l holds the VPL consecutive voxels k0 + VPL*l ...; VPL = 2, 4, 8 or
-// 16, chosen by the autotuner: the kernel is issue bound, and the per-column
-// setup below is paid once per lane for VPL voxels).  Everything that depends only on
-// (i, j) and the view -- the candidate columns within hwu of the voxel
-// column's projection, each column's family, plane m, exact in-plane weight
-// wb (from the same Q.40 crossing K1 uses) and vertical step -- is uniform
-// over the warp.  Per voxel, the detector rows that can reach it lie among the
-// ntap rows starting at the first row of its vertical footprint.  For a
-// lane's first voxel the offset q_z - k of that row is taken exactly from the
-// Q.40 crossing; the next rows follow by the per-row step, and the next voxel
-// by subtracting one and dropping the rows that fell below its footprint, so
-// wz = max(0, 1 - |q_z - k|) is accurate to about 1e-6.  A column whose rows
-// are spaced by `step` voxels reaches a voxel with at most
-// floor(2 / step * (1 + 1e-4) + 0.002) + 1 rows; columns that need fewer than
-// the geometry's ntap take a loop one or two taps shorter, and columns whose
-// windows all stay inside the zero pads skip the clamp (warp-uniform branches).  The residual arrives transposed and zero-padded
-// (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight W), so the
-// lanes' row reads are contiguous and need no bounds test.  The gradient is
-// written in z-innermost order [j][i][k], coalesced.
+// 16), or of a 2x2 group of such columns (VPL = 4 or 8), chosen by the
+// autotuner: the kernel is issue bound, and the per-column setup below is
+// paid once per lane for VPL voxels.  Everything that depends only on (i, j)
+// and the view -- the candidate columns within hwu of the voxel column's
+// projection, each column's family, plane m, exact in-plane weight wb (from
+// the same Q.40 crossing K1 uses) and vertical step -- is uniform over the
+// warp.  Along z the kernel forms the column's z-profile, the transpose of
+// K1's linear interpolation: the rows of the column cross plane m at q_z =
+// q_z(first) + t*step, and a row whose crossing lies in the unit cell
+// [k, k + 1) at fraction f gives (1 - f) r to voxel k and f r to voxel k + 1.
+// A lane walks the cells kfirst - 1 .. kfirst + VPL - 1 in order, taking each
+// row once (at most C = ceil(1 / step) rows per cell, a warp-uniform template
+// choice); the offset of the lane's first row is exact from the Q.40
+// crossing and the next ones follow by the per-row step, so the weights are
+// accurate to about 1e-6.  Columns whose cells all stay inside the zero pads
+// skip the clamp (a warp vote).  The residual arrives transposed and
+// zero-padded (rt[s][iu][RT_PAD + iv], already multiplied by K1's row weight
+// W), so the lanes' row reads are contiguous and need no bounds test.  The
+// gradient is written in z-innermost order [j][i][k], coalesced.
 #include "fbl_internal.cuh"
 #include "fbl_reduce.cuh"
 
@@ -38,8 +39,7 @@ constexpr int K2_LANES = 32;
 // Launch configuration of the backprojector: k2_vpl in {2, 4, 8, 16} is one
 // voxel column per warp with that many consecutive voxels per lane; 24 and 28
 // are a 2x2 group of voxel columns per warp (k2_tile22) with 4 or 8 voxels per
-// lane in each.  The batched kernel runs a group volume with one column per
-// warp and the same voxels per lane (the sums are the same).
+// lane in each (the same sums, bit for bit).
 __host__ __device__ __forceinline__ bool k2_group_of(const DevGeom &g) { return g.k2_vpl == 24 || g.k2_vpl == 28; }
 __host__ __device__ __forceinline__ int k2_vpl_of(const DevGeom &g) {
     if (k2_group_of(g)) return g.k2_vpl - 20;
@@ -57,110 +57,89 @@ struct BpArgs {
     double *g2_partials;  // optional: per-block sum of the squared gradient
 };
 
-// Drop the rows that fell below the next voxel's footprint: while d0 <= -1,
-// one row up (lo and r advance together; the caller uses one of them).  A
-// column reached by at most NT rows per voxel has rows spaced step > 2/NT
-// apart, so a voxel drops at most (NT + 1) / 2 rows: that many predicated
-// steps, no data-dependent loop, so the compiler can overlap the taps of
-// consecutive voxels.  The same additions as the loop, in the same order.
-template <int NT>
-__device__ __forceinline__ void advance_window(float &d0, float step, int &lo, const float *&r) {
-#pragma unroll
-    for (int c = 0; c < (NT + 1) / 2; ++c) {
-        const bool p = d0 <= -1.f;
-        d0 = p ? d0 + step : d0;
-        lo += p ? 1 : 0;
-        r += p ? 1 : 0;
-    }
-}
-
-// The taps of one candidate column for the lane's VPL voxels: window of NT
-// rows from `lo`, whose first crossing lies d0 voxels from the lane's first
-// voxel (-1 < d0 <= -1 + step).  After each voxel the window drops the rows
-// that fell below the next voxel's footprint.  CLAMP: keep each window inside
-// the zero pads (needed only when a lane's windows could leave them; a window
-// clamped into the pads holds no real row since ntap <= RT_PAD).
-template <int NT, int VPL, bool CLAMP>
-__device__ __forceinline__ void column_taps(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
-                                            int lo, float d0, float step, int lo_max) {
+// The z-profile of one candidate column over the lane's VPL voxels, by unit
+// cells: cell c = [k, k + 1) of the z axis holds the rows whose crossing q_z
+// lies in it; a row at fraction f = q_z - k gives (1 - f) r to voxel k and
+// f r to voxel k + 1 (the transpose of K1's linear interpolation along z).
+// The lane walks cells kfirst - 1 .. kfirst + VPL - 1 (VPL + 1 cells) with
+// e = q_z(first row not yet taken) - k, in [0, step] (a row on a cell
+// boundary may be taken by either cell: f = 1 in the lower cell gives the
+// same two weights as f = 0 in the upper one).  C = 1: rows more than one
+// voxel apart, at most one per cell, tested.  C >= 2: rows at most one voxel
+// apart (step <= 1), so the first row is always in the cell, and at most C
+// rows per cell, the others tested.  add(q, P) receives voxel q's profile
+// value.  CLAMP as for the windows: a window outside [-RT_PAD, lo_max] holds
+// only zero rows.
+template <int C, int VPL, bool CLAMP, class Add>
+__device__ __forceinline__ void column_cells(Add add, const float *__restrict__ rcol, int lo, float e,
+                                             float step, int lo_max) {
     const float *r = rcol + lo;
+    float carry = 0.f;
 #pragma unroll
-    for (int q = 0; q < VPL; ++q) {
+    for (int c = 0; c <= VPL; ++c) {
         const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
-        float sz = 0.f;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const float d = fmaf((float)t, step, d0);
-            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(w + t), sz);
+        bool v[C];
+        float s0, s1;
+        {
+            const float r0 = __ldg(w);
+            v[0] = C > 1 ? true : e < 1.f;
+            const float rv = v[0] ? r0 : 0.f;
+            s0 = rv;
+            s1 = e * rv;
         }
-        acc[q] = fmaf(wb, sz, acc[q]);
-        // next voxel up: same rows sit one voxel lower; drop rows now below k - 1
-        d0 -= 1.f;
-        advance_window<NT>(d0, step, lo, r);
+#pragma unroll
+        for (int t = 1; t < C; ++t) {
+            const float et = fmaf((float)t, step, e);
+            v[t] = et < 1.f;
+            const float rv = v[t] ? __ldg(w + t) : 0.f;
+            s0 += rv;
+            s1 = fmaf(et, rv, s1);
+        }
+        if (c >= 1) add(c - 1, carry + (s0 - s1));
+        carry = s1;
+        if (c == VPL) break;
+        // next cell: e of the first row not taken, minus one
+        float en = fmaf((float)C, step, e);
+#pragma unroll
+        for (int t = C - 1; t >= 0; --t) en = v[t] ? en : fmaf((float)t, step, e);
+        e = en - 1.f;
+        int n = 0;
+#pragma unroll
+        for (int t = 0; t < C; ++t) n += v[t] ? 1 : 0;
+        r += n;
+        lo += n;
     }
 }
 
-// Taps of one column: this column's own tap count floor(2 inv) + 1 (the
-// geometry's NTAP, or one or two fewer: rows spaced wider than the geometry's
-// closest), and the clamp-free form when every lane's windows stay inside the
-// pads (a warp vote; all lanes are active).  A window with more taps than
-// needed gives the same sums (the extra taps weigh exactly 0).
-template <int NTAP, int VPL, bool CLAMP>
-__device__ __forceinline__ void column_taps_nt(int nt, float (&acc)[VPL], float wb,
-                                               const float *__restrict__ rcol, int lo, float d0, float step,
-                                               int lo_max) {
-    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
-    constexpr int NT2 = NTAP > 2 ? NTAP - 2 : NT1;
-    if (nt <= NT2) column_taps<NT2, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
-    else if (nt <= NT1) column_taps<NT1, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
-    else column_taps<NTAP, VPL, CLAMP>(acc, wb, rcol, lo, d0, step, lo_max);
+// Dispatch on the column's row spacing: one row per cell at most (step > 1),
+// else the geometry's largest rows-per-cell bound or one less.
+template <int NTAP, int VPL, bool CLAMP, class Add>
+__device__ __forceinline__ void column_cells_c(int cc, float step, Add add, const float *__restrict__ rcol, int lo,
+                                               float e, int lo_max) {
+    constexpr int CM = (NTAP + 1) / 2;
+    constexpr int CM1 = CM > 2 ? CM - 1 : 2;
+    if (CM < 2 || step > 1.f) column_cells<1, VPL, CLAMP>(add, rcol, lo, e, step, lo_max);
+    else if (CM > 2 && cc <= CM1) column_cells<CM1, VPL, CLAMP>(add, rcol, lo, e, step, lo_max);
+    else column_cells<(CM < 2 ? 2 : CM), VPL, CLAMP>(add, rcol, lo, e, step, lo_max);
 }
 
+// Rows per cell of a column (an upper bound: the geometry's ntap is
+// floor(2 x) + 1 and this floor(x) + 1 with the same x).
+__device__ __forceinline__ int cells_rows(float inv) { return (int)(inv * 1.0001f + 0.001f) + 1; }
+
+// One candidate column's z-profile over the lane's VPL voxels, added to acc
+// with the in-plane weight wb; lo and d0 = q_z(lo) - kfirst in (-1, -1 + step]
+// locate the lane's first row.
 template <int NTAP, int VPL>
-__device__ __forceinline__ void column_taps_any(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
+__device__ __forceinline__ void column_profile(float (&acc)[VPL], float wb, const float *__restrict__ rcol,
                                                 int lo, float d0, float step, float inv, int lo_max) {
-    const int nt = (int)(2.f * inv * 1.0001f + 0.002f) + 1;
+    const int cc = cells_rows(inv);
     const bool inside = lo >= -RT_PAD && lo + (int)((float)VPL * inv) + 2 <= lo_max;
+    auto add = [&](int q, float P) { acc[q] = fmaf(wb, P, acc[q]); };
     if (__all_sync(0xffffffffu, inside))
-        column_taps_nt<NTAP, VPL, false>(nt, acc, wb, rcol, lo, d0, step, lo_max);
+        column_cells_c<NTAP, VPL, false>(cc, step, add, rcol, lo, d0 + 1.f, lo_max);
     else
-        column_taps_nt<NTAP, VPL, true>(nt, acc, wb, rcol, lo, d0, step, lo_max);
-}
-
-// column_taps for a z-profile that two voxel columns share: the same window,
-// taps and advance, with sz accumulated into both as fmaf(w, sz, acc) (a zero
-// weight leaves an accumulator's bits unchanged: acc is never -0 and sz is
-// finite).
-template <int NT, int VPL, bool CLAMP>
-__device__ __forceinline__ void column_taps2(float (&accA)[VPL], float (&accB)[VPL], float wA, float wB,
-                                             const float *__restrict__ rcol, int lo, float d0, float step,
-                                             int lo_max) {
-    const float *r = rcol + lo;
-#pragma unroll
-    for (int q = 0; q < VPL; ++q) {
-        const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
-        float sz = 0.f;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const float d = fmaf((float)t, step, d0);
-            sz = fmaf(fmaxf(0.f, 1.f - fabsf(d)), __ldg(w + t), sz);
-        }
-        accA[q] = fmaf(wA, sz, accA[q]);
-        accB[q] = fmaf(wB, sz, accB[q]);
-        d0 -= 1.f;
-        advance_window<NT>(d0, step, lo, r);
-    }
-}
-
-template <int NTAP, int VPL, bool CLAMP>
-__device__ __forceinline__ void column_taps2_nt(int nt, float (&accA)[VPL], float (&accB)[VPL], float wA, float wB,
-                                                const float *__restrict__ rcol, int lo, float d0, float step,
-                                                int lo_max) {
-    constexpr int NT1 = NTAP > 1 ? NTAP - 1 : 1;
-    constexpr int NT2 = NTAP > 2 ? NTAP - 2 : NT1;
-    if (nt <= NT2) column_taps2<NT2, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
-    else if (nt <= NT1) column_taps2<NT1, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
-    else column_taps2<NTAP, VPL, CLAMP>(accA, accB, wA, wB, rcol, lo, d0, step, lo_max);
+        column_cells_c<NTAP, VPL, true>(cc, step, add, rcol, lo, d0 + 1.f, lo_max);
 }
 
 // The first row of one (column, plane) window for the lane's first voxel:
@@ -226,12 +205,16 @@ __device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevG
         const ZWin zw = z_window(g, cF, m, kfirst);
         float(&a0)[VPL] = acc[FAMY ? 0 : p][FAMY ? p : 0];
         float(&a1)[VPL] = acc[FAMY ? 1 : p][FAMY ? p : 1];
-        const int nt = (int)(2.f * zw.inv * 1.0001f + 0.002f) + 1;
+        const int cc = cells_rows(zw.inv);
         const bool inside = zw.lo >= -RT_PAD && zw.lo + (int)((float)VPL * zw.inv) + 2 <= lo_max;
+        auto add = [&](int q, float P) {
+            a0[q] = fmaf(w0, P, a0[q]);
+            a1[q] = fmaf(w1, P, a1[q]);
+        };
         if (__all_sync(0xffffffffu, inside))
-            column_taps2_nt<NTAP, VPL, false>(nt, a0, a1, w0, w1, rcol, zw.lo, zw.d0, zw.step, lo_max);
+            column_cells_c<NTAP, VPL, false>(cc, zw.step, add, rcol, zw.lo, zw.d0 + 1.f, lo_max);
         else
-            column_taps2_nt<NTAP, VPL, true>(nt, a0, a1, w0, w1, rcol, zw.lo, zw.d0, zw.step, lo_max);
+            column_cells_c<NTAP, VPL, true>(cc, zw.step, add, rcol, zw.lo, zw.d0 + 1.f, lo_max);
     }
 }
 
@@ -367,7 +350,7 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
                 d0 -= step;
             }
             const float *rcol = a.rt + ((size_t)s * g.nu + iu) * rp + RT_PAD;
-            column_taps_any<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, inv, lo_max);
+            column_profile<NTAP, K2_VPL>(acc, wb, rcol, lo, d0, step, inv, lo_max);
         }
     }
     float g2 = 0.f;
@@ -392,9 +375,10 @@ __device__ __forceinline__ void k2_tile(const BpArgs &a, int bx, int j, int bz, 
 }
 
 template <int NTAP, int K2_VPL>
-// At most 48 registers (5 blocks per SM); measured against the compiler's own
-// choices (40, and 92-168 with one block per SM): 14.47 against 14.68 and
-// 18.9 ms per 40-view launch at 512^3 with 8 voxels per lane.
+// At most 48 registers (5 blocks per SM); with the per-voxel tap loop this
+// kernel had before the cell walk, that cap measured 14.47 ms per 40-view
+// launch at 512^3 (8 voxels per lane) against 14.68 and 18.9 ms with the
+// compiler's own choices (40 registers, and 92-168 with one block per SM).
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) k2_backproject(const BpArgs a) {
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     k2_tile<NTAP, K2_VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
