@@ -21,7 +21,8 @@
 // planes at a time, into a shared-memory table (plane and row folded into one
 // element offset, and the fraction) that every sample reads with one
 // broadcast load; a sample then costs one 64-bit add and a funnel shift for
-// its vertical crossing, a clamp, four loads and three interpolations.  Each
+// its vertical crossing, one unsigned minimum (the clamp), four loads and
+// three interpolations (the two in-plane ones as one packed FP32x2 FMA).  Each
 // ray's plane interval [m0, m1] is the exact set of planes whose crossing lies
 // inside (-1, Nb) x (-1, nz) (an interval: the maps are affine in m); the warp
 // walks the union of its rays' intervals with no per-sample mask: the
@@ -105,6 +106,21 @@ __device__ __forceinline__ void plane_range(const RayConst &rc, int Na, int &m0,
     m1 = c;
 }
 
+// The two in-plane interpolations of a sample, lo = a0 + f (b0 - a0) and
+// hi = a1 + f (b1 - a1), as one packed FP32x2 subtraction and one packed FMA
+// (the same roundings as two fmaf(f, b - a, a)).
+__device__ __forceinline__ void lerp2(float f, float a0, float a1, float b0, float b1, float &lo, float &hi) {
+    asm("{\n\t.reg .b64 a, b, c, d;\n\t"
+        "mov.b64 a, {%2, %3};\n\t"
+        "mov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 b, b, a;\n\t"
+        "mov.b64 c, {%6, %6};\n\t"
+        "fma.rn.f32x2 d, c, b, a;\n\t"
+        "mov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(lo), "=f"(hi)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(f));
+}
+
 // Planes per in-plane table chunk: one entry per lane.
 constexpr int K1_CHUNK = 32;
 
@@ -114,9 +130,11 @@ constexpr int K1_CHUNK = 32;
 // crossing at plane mb in Q.32 (advanced to mb + len).  The warp walks the
 // union of its rays' intervals, and the in-plane crossing is common to the
 // column, so a sample outside its own ray's interval lies below or above the
-// volume in z: its row k0 is clamped to [-2, nz], where both taps read the two
-// zero elements each z-row carries at either end, and it adds exactly +0 --
-// no mask.  Samples with j even go to s0, odd to s1, each in plane order.
+// volume in z: its row is clamped to the zero elements each z-row carries at
+// either end (qz and the table offsets are shifted by 2 rows, so one unsigned
+// minimum sends rows below -2 to the two zeros above nz and rows above nz to
+// them too), and it adds exactly +0 -- no mask.  Samples with j even go to s0,
+// odd to s1, each in plane order.
 // PIPE: the next sample's loads are issued before the current sample is
 // interpolated (same operations, same order per partial sum).
 template <bool PIPE, typename TX>
@@ -127,10 +145,12 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
     };
     auto fetch = [&](int j, Smp &o) {
         const int2 e = tab[j];
-        const int k0 = min(max(fx32_floor(qz), -2), nz);
+        // qz carries +2: k0 + 2 as unsigned, clamped to nz + 2 (rows below -2
+        // wrap to the top: both ends hold two zero elements); e.x carries -2
+        const unsigned k2 = min((unsigned)fx32_floor(qz), (unsigned)(nz + 2));
         o.fz = fx32_frac(qz);
         qz += qz1;
-        const TX *p = vol + (e.x + k0);
+        const TX *p = vol + (e.x + (int)k2);
         o.fb = __int_as_float(e.y);
         o.v00 = ldg_f32(p);
         o.v10 = ldg_f32(p + 1);
@@ -138,8 +158,8 @@ __device__ __forceinline__ void chunk_loop(const TX *__restrict__ vol, const int
         o.v11 = ldg_f32(p + bs + 1);
     };
     auto value = [](const Smp &o) {
-        const float lo = fmaf(o.fb, o.v01 - o.v00, o.v00);
-        const float hi = fmaf(o.fb, o.v11 - o.v10, o.v10);
+        float lo, hi;
+        lerp2(o.fb, o.v00, o.v10, o.v01, o.v11, lo, hi);
         return fmaf(o.fz, hi - lo, lo);
     };
     if (!PIPE) {
@@ -278,13 +298,14 @@ __device__ __forceinline__ void k1_tile(const ProjArgs &a, int cb, int s, int ba
             // the vertical crossing in Q.32 from the warp's first plane (ray_z32)
             long long qz, qz1;
             ray_z32(rc, u0, qz, qz1);
+            qz += 2LL << 32;  // chunk_loop's row index is k0 + 2
             float s0 = 0.f, s1 = 0.f;
             for (int mb = u0; mb <= u1; mb += K1_CHUNK) {
                 const int len = min(K1_CHUNK, u1 - mb + 1);
                 {
                     const int m = min(mb + lane, u1);
                     const long long qb = rc.qb0 + (long long)m * rc.qb1;
-                    tab[lane] = make_int2(base + m * ps + fx_floor(qb) * bs, __float_as_int(fx_frac(qb)));
+                    tab[lane] = make_int2(base - 2 + m * ps + fx_floor(qb) * bs, __float_as_int(fx_frac(qb)));
                 }
                 __syncwarp();
                 // the store mode always issues loads one sample ahead; the residual
@@ -578,7 +599,7 @@ __global__ void __launch_bounds__(32 * TMA_COLS) k1_project_tma(const ProjArgs a
         for (int m = pa; m <= pb; ++m) {
             const int b0 = fx_floor(qb);
             const float fb = fx_frac(qb);
-            // k1_tile's clamp: outside its ray's interval a sample reads zero elements
+            // as in k1_tile, a sample outside its ray's interval reads zero elements
             const int k0 = min(max(fx32_floor(qz), -2), g.nz);
             const float fz = fx32_frac(qz);
             float v00, v10, v01, v11;
