@@ -57,6 +57,65 @@ struct BpArgs {
     double *g2_partials;  // optional: per-block sum of the squared gradient
 };
 
+// Packed FP32x2 arithmetic (sm_100 family): the same IEEE operation on each
+// half, so results equal two scalar operations bit for bit.
+__device__ __forceinline__ void pk_mul(float ax, float ay, float bx, float by, float &dx, float &dy) {
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(dx), "=f"(dy) : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+__device__ __forceinline__ void pk_add(float ax, float ay, float bx, float by, float &dx, float &dy) {
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "add.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(dx), "=f"(dy) : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+__device__ __forceinline__ void pk_sub(float ax, float ay, float bx, float by, float &dx, float &dy) {
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(dx), "=f"(dy) : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+__device__ __forceinline__ void pk_fma(float ax, float ay, float bx, float by, float cx, float cy, float &dx,
+                                       float &dy) {
+    asm("{\n\t.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(dx), "=f"(dy) : "f"(ax), "f"(ay), "f"(bx), "f"(by), "f"(cx), "f"(cy));
+}
+
+// One cell's rows: r[t] the row values already masked (0 where the row is not
+// in the cell), et[t] their offsets from the cell's bottom; then the walk
+// moves to the next cell.
+template <int C, bool CLAMP>
+struct CellRows {
+    float r[C], et[C];
+    __device__ __forceinline__ void load(const float *__restrict__ rcol, int &lo, float &e, float step, int lo_max) {
+        // a 32-bit row index, the address formed per cell (cheaper than stepping
+        // a 64-bit pointer by the data-dependent row count)
+        const float *w = rcol + (CLAMP ? min(max(lo, -RT_PAD), lo_max) : lo);
+        bool v[C];
+        et[0] = e;
+        v[0] = C > 1 ? true : e < 1.f;
+        {
+            const float r0 = __ldg(w);
+            r[0] = v[0] ? r0 : 0.f;
+        }
+#pragma unroll
+        for (int t = 1; t < C; ++t) {
+            et[t] = fmaf((float)t, step, e);
+            v[t] = et[t] < 1.f;
+            r[t] = v[t] ? __ldg(w + t) : 0.f;
+        }
+        // next cell: e of the first row not taken, minus one
+        float en = fmaf((float)C, step, e);
+#pragma unroll
+        for (int t = C - 1; t >= 0; --t) en = v[t] ? en : fmaf((float)t, step, e);
+        e = en - 1.f;
+        int n = 0;
+#pragma unroll
+        for (int t = 0; t < C; ++t) n += v[t] ? 1 : 0;
+        lo += n;
+    }
+};
+
 // The z-profile of one candidate column over the lane's VPL voxels, by unit
 // cells: cell c = [k, k + 1) of the z axis holds the rows whose crossing q_z
 // lies in it; a row at fraction f = q_z - k gives (1 - f) r to voxel k and
@@ -67,47 +126,40 @@ struct BpArgs {
 // same two weights as f = 0 in the upper one).  C = 1: rows more than one
 // voxel apart, at most one per cell, tested.  C >= 2: rows at most one voxel
 // apart (step <= 1), so the first row is always in the cell, and at most C
-// rows per cell, the others tested.  add(q, P) receives voxel q's profile
-// value.  CLAMP as for the windows: a window outside [-RT_PAD, lo_max] holds
-// only zero rows.
-template <int C, int VPL, bool CLAMP, class Add>
-__device__ __forceinline__ void column_cells(Add add, const float *__restrict__ rcol, int lo, float e,
+// rows per cell, the others tested.  The cells of voxels q and q + 1 are
+// loaded one after the other and their sums formed with packed FP32x2
+// operations; add2(q, P_q, P_q+1) receives the two voxels' profile values.
+// CLAMP as for the windows: a window outside [-RT_PAD, lo_max] holds only
+// zero rows.
+template <int C, int VPL, bool CLAMP, class Add2>
+__device__ __forceinline__ void column_cells(Add2 add2, const float *__restrict__ rcol, int lo, float e,
                                              float step, int lo_max) {
-    float carry = 0.f;
+    float carry;
+    {  // cell kfirst - 1: only its f part, to voxel 0
+        CellRows<C, CLAMP> a;
+        a.load(rcol, lo, e, step, lo_max);
+        float s1 = a.et[0] * a.r[0];
 #pragma unroll
-    for (int c = 0; c <= VPL; ++c) {
-        // a 32-bit row index, the address formed per cell (cheaper than stepping
-        // a 64-bit pointer by the data-dependent row count)
-        const float *w = rcol + (CLAMP ? min(max(lo, -RT_PAD), lo_max) : lo);
-        bool v[C];
-        float s0, s1;
-        {
-            const float r0 = __ldg(w);
-            v[0] = C > 1 ? true : e < 1.f;
-            const float rv = v[0] ? r0 : 0.f;
-            s0 = rv;
-            s1 = e * rv;
-        }
+        for (int t = 1; t < C; ++t) s1 = fmaf(a.et[t], a.r[t], s1);
+        carry = s1;
+    }
+#pragma unroll
+    for (int q = 0; q < VPL; q += 2) {  // the cells of voxels q and q + 1, two at a time
+        CellRows<C, CLAMP> a, b;
+        a.load(rcol, lo, e, step, lo_max);
+        b.load(rcol, lo, e, step, lo_max);
+        float s0a = a.r[0], s0b = b.r[0], s1a, s1b;
+        pk_mul(a.et[0], b.et[0], a.r[0], b.r[0], s1a, s1b);
 #pragma unroll
         for (int t = 1; t < C; ++t) {
-            const float et = fmaf((float)t, step, e);
-            v[t] = et < 1.f;
-            const float rv = v[t] ? __ldg(w + t) : 0.f;
-            s0 += rv;
-            s1 = fmaf(et, rv, s1);
+            pk_add(s0a, s0b, a.r[t], b.r[t], s0a, s0b);
+            pk_fma(a.et[t], b.et[t], a.r[t], b.r[t], s1a, s1b, s1a, s1b);
         }
-        if (c >= 1) add(c - 1, carry + (s0 - s1));
-        carry = s1;
-        if (c == VPL) break;
-        // next cell: e of the first row not taken, minus one
-        float en = fmaf((float)C, step, e);
-#pragma unroll
-        for (int t = C - 1; t >= 0; --t) en = v[t] ? en : fmaf((float)t, step, e);
-        e = en - 1.f;
-        int n = 0;
-#pragma unroll
-        for (int t = 0; t < C; ++t) n += v[t] ? 1 : 0;
-        lo += n;
+        float da, db, Pa, Pb;
+        pk_sub(s0a, s0b, s1a, s1b, da, db);
+        pk_add(carry, s1a, da, db, Pa, Pb);
+        add2(q, Pa, Pb);
+        carry = s1b;
     }
 }
 
@@ -135,7 +187,7 @@ __device__ __forceinline__ void column_profile(float (&acc)[VPL], float wb, cons
                                                 int lo, float d0, float step, float inv, int lo_max) {
     const int cc = cells_rows(inv);
     const bool inside = lo >= -RT_PAD && lo + (int)((float)VPL * inv) + 2 <= lo_max;
-    auto add = [&](int q, float P) { acc[q] = fmaf(wb, P, acc[q]); };
+    auto add = [&](int q, float Pa, float Pb) { pk_fma(wb, wb, Pa, Pb, acc[q], acc[q + 1], acc[q], acc[q + 1]); };
     if (__all_sync(0xffffffffu, inside))
         column_cells_c<NTAP, VPL, false>(cc, step, add, rcol, lo, d0 + 1.f, lo_max);
     else
@@ -207,9 +259,9 @@ __device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevG
         float(&a1)[VPL] = acc[FAMY ? 1 : p][FAMY ? p : 1];
         const int cc = cells_rows(zw.inv);
         const bool inside = zw.lo >= -RT_PAD && zw.lo + (int)((float)VPL * zw.inv) + 2 <= lo_max;
-        auto add = [&](int q, float P) {
-            a0[q] = fmaf(w0, P, a0[q]);
-            a1[q] = fmaf(w1, P, a1[q]);
+        auto add = [&](int q, float Pa, float Pb) {
+            pk_fma(w0, w0, Pa, Pb, a0[q], a0[q + 1], a0[q], a0[q + 1]);
+            pk_fma(w1, w1, Pa, Pb, a1[q], a1[q + 1], a1[q], a1[q + 1]);
         };
         if (__all_sync(0xffffffffu, inside))
             column_cells_c<NTAP, VPL, false>(cc, zw.step, add, rcol, zw.lo, zw.d0 + 1.f, lo_max);
