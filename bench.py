@@ -42,9 +42,10 @@ UNIT = "GUPS"
 # Algorithmic FP32 operations.  A Joseph sample of K1 (one ray, one plane):
 # 3 linear interpolations of 2 operations, 1 accumulation and the 2
 # coordinate steps along the ray, plus the 2 fractions of the crossing (10).
-# Each in-volume sample is 4 nonzeros of A; K2 spends, per nonzero, the tap
-# weight 1 - |d|, its product with the in-plane weight, the accumulation
-# and the step to the next row (4), so 16 per in-volume sample.
+# Each in-volume sample is 4 nonzeros of A; the transpose costs, per nonzero,
+# its vertical weight (1 - f or f of the row's crossing), its product with
+# the in-plane weight, the accumulation and the step to the next row (4), so
+# 16 per in-volume sample, whatever order K2 visits them in.
 K1_OPS_PER_SAMPLE = 10
 K2_OPS_PER_SAMPLE = 16
 K3_BYTES_PER_VOXEL = 12  # read x and g, write x_bar (FP32)
