@@ -411,10 +411,19 @@ def paper_cases_record(fbl, device, budget_s=30.0, mu_fraction=None):
             bb = b16 if fast else b
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            el, k, hist = 0.0, 0, []
+            el, k, hist, stopped = 0.0, 0, [], None
             while el < budget_s and k < 5000:
                 e0.record(stream)
-                S.step(x, bb)
+                try:
+                    S.step(x, bb)
+                except fbl.FblError as ex:
+                    # e.g. no trial passes (2.3) within the backtrack cap: the
+                    # solver keeps x; the method stops here
+                    torch.cuda.synchronize(device)
+                    stopped = {"iteration": k + 1, "seconds": el, "error": str(ex)}
+                    F, _, re = fbl.evaluate(G, x.float(), b, mu, x_true=xt_d)
+                    hist.append((el, k, F, re))
+                    break
                 e1.record(stream)
                 torch.cuda.synchronize(device)
                 el += e0.elapsed_time(e1) * 1e-3
@@ -423,6 +432,8 @@ def paper_cases_record(fbl, device, budget_s=30.0, mu_fraction=None):
                     F, _, re = fbl.evaluate(G, x.float(), b, mu, x_true=xt_d)
                     hist.append((el, k, F, re))
             rec = {"iterations": k, "ms_per_iteration": 1e3 * el / max(k, 1)}
+            if stopped:
+                rec["stopped"] = stopped
             for t in (budget_s / 4, budget_s / 2, budget_s):
                 last = [h for h in hist if h[0] <= t]
                 if last:

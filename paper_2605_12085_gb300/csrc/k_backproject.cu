@@ -258,7 +258,8 @@ __device__ __forceinline__ void group_column(float (&acc)[2][2][VPL], const DevG
         float(&a0)[VPL] = acc[FAMY ? 0 : p][FAMY ? p : 0];
         float(&a1)[VPL] = acc[FAMY ? 1 : p][FAMY ? p : 1];
         const int cc = cells_rows(zw.inv);
-        const bool inside = zw.lo >= -RT_PAD && zw.lo + (int)((float)VPL * zw.inv) + 2 <= lo_max;
+        // rows per voxel < ntap / 2 on every column of the geometry
+        const bool inside = zw.lo >= -RT_PAD && zw.lo + (VPL * NTAP + 1) / 2 + 2 <= lo_max;
         auto add = [&](int q, float Pa, float Pb) {
             pk_fma(w0, w0, Pa, Pb, a0[q], a0[q + 1], a0[q], a0[q + 1]);
             pk_fma(w1, w1, Pa, Pb, a1[q], a1[q + 1], a1[q], a1[q + 1]);
@@ -292,8 +293,9 @@ __device__ __forceinline__ void k2_tile22(const BpArgs &a, int gx, int gy, int b
     for (int s = 0; s < nsel; ++s) {
         const int v = a.views[s];
         const float2 cs = g.trig[v];
-        // the union of the four voxel columns' candidate windows (k2_tile's)
-        int iu_lo = g.nu, iu_hi = -1;
+        // the union of the four voxel columns' candidate windows (k2_tile's),
+        // from the extreme projections (ceil and floor are monotone)
+        float umin = 3.0e38f, umax = -3.0e38f;
 #pragma unroll
         for (int x = 0; x < 2; ++x)
 #pragma unroll
@@ -303,9 +305,11 @@ __device__ __forceinline__ void k2_tile22(const BpArgs &a, int gx, int gy, int b
                 const float xi = xc * cs.x + yc * cs.y;
                 const float eta = -xc * cs.y + yc * cs.x;
                 const float iuc = eta * __fdividef(g.sdd, g.sod - xi) * g.inv_du + g.cu;
-                iu_lo = min(iu_lo, max(0, (int)ceilf(iuc - g.hwu)));
-                iu_hi = max(iu_hi, min(g.nu - 1, (int)floorf(iuc + g.hwu)));
+                umin = fminf(umin, iuc);
+                umax = fmaxf(umax, iuc);
             }
+        const int iu_lo = max(0, (int)ceilf(umin - g.hwu));
+        const int iu_hi = min(g.nu - 1, (int)floorf(umax + g.hwu));
         for (int iu = iu_lo; iu <= iu_hi; ++iu) {
             const size_t col = (size_t)v * g.nu + iu;
             const FxCol *cF = g.colF + col;

@@ -230,17 +230,21 @@ template <typename TX, typename TB, typename TO, int MODE>
 __device__ __forceinline__ void epilogue(const ProjArgs &a, const float4 &cB, int s, int iu, int iv,
                                          float w, float sum, float &r2) {
     const DevGeom &g = a.g;
-    const float W = cB.x * sqrtf(fmaf(w, w, cB.y));  // the row weight v_a |d| / |d_a|
-    const float ax = W * sum;
+    // Explicitly rounded operations: the compiler may not contract them into
+    // FMAs, so the residual and objective modes (separate instantiations)
+    // give the same r and r^2 for the same point, bit for bit -- the line
+    // search compares f_N(x) from one with f_N(x_bar) from the other.
+    const float W = __fmul_rn(cB.x, sqrtf(__fmaf_rn(w, w, cB.y)));  // the row weight v_a |d| / |d_a|
+    const float ax = __fmul_rn(W, sum);
     if (MODE == PROJ_STORE) {
         ((TO *)a.out)[((size_t)s * g.nv + iv) * g.nu + iu] = from_f32<TO>(ax);
     } else {
         const int bv = a.b_views ? a.b_views[s] : s;
         const float bval = ldg_f32((const TB *)a.b + ((size_t)bv * g.nv + iv) * g.nu + iu);
-        const float r = ax - bval;
+        const float r = __fsub_rn(ax, bval);
         if (MODE == PROJ_RESID)
-            ((float *)a.out)[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = W * r;
-        r2 += r * r;
+            ((float *)a.out)[((size_t)s * g.nu + iu) * rt_pitch(g.nv) + RT_PAD + iv] = __fmul_rn(W, r);
+        r2 = __fmaf_rn(r, r, r2);
     }
 }
 
