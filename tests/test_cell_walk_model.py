@@ -4,10 +4,12 @@ candidate column, k_backproject.cu), checked on the CPU.
 The kernel takes the detector rows of a column in order through the unit
 cells kfirst - 1 .. kfirst + VPL - 1 of a lane's voxels. It holds at most C
 rows per cell, and it skips the clamp when the first row lo satisfies
-lo + (VPL * ntap + 1) / 2 + 2 <= nv + RT_PAD - ntap. This model repeats the
+lo + (VPL * ntap + 1) / 2 + 2 <= nv + RT_PAD - ntap (2x2-group kernel) or
+lo + floor(VPL * rows per voxel) + 2 <= nv + RT_PAD - ntap (one-column
+kernel). This model repeats the
 walk's float32 arithmetic and row bookkeeping, and checks three things:
 
-* every row it reads lies within that bound, so the clamp-free loads stay
+* every row it reads lies within both bounds, so the clamp-free loads stay
   inside the zero-padded residual rows;
 * its profile equals the direct sum of the interpolation weights
   max(0, 1 - |q_z - k|) r over all rows (the transpose of K1's linear
@@ -106,10 +108,13 @@ def test_cell_walk_bounds_and_values(vpl):
             d0 = f32(-1 + step)
         rows = rng.standard_normal(4 * vpl + 64).astype(f32)
         prof, read, taken = walk(rows, 0, d0, step, vpl, C)
-        # reads against the clamp-free bound, relative to the first row
+        # reads against the clamp-free bounds, relative to the first row: the
+        # 2x2-group kernel's (from the geometry's ntap) and the one-column
+        # kernel's (from the column's own rows per voxel), both minus ntap - 1
         bound = (vpl * ntap + 1) // 2 + 2 + ntap - 1
-        worst_margin = max(worst_margin, max(read) - bound)
-        assert max(read) <= bound, (step, d0, vpl, C, max(read), bound)
+        bound1 = int(f32(f32(vpl) * inv)) + 2 + ntap - 1
+        worst_margin = max(worst_margin, max(read) - min(bound, bound1))
+        assert max(read) <= min(bound, bound1), (step, d0, vpl, C, max(read), bound, bound1)
         assert min(read) >= 0
         # every row of the walk's range taken once, in order
         assert taken == list(range(len(taken)))
