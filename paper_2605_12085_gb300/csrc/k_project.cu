@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(32 * COLS, 48 / COLS) kb_project(const BatchHd
     __shared__ int s_tile;
     __shared__ ProjArgs sa;
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    // the trial objective covers this round's searching volumes only
+    // the trial objective covers only the volumes still searching in this trial
     const int total = MODE == PROJ_NORM ? hdr->rtotal[0] : hdr->total[0];
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(ctr, 1);
