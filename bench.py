@@ -738,9 +738,19 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None, de
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         n_iter = sum(it for _, it in fbl.fbl_schedule(g.n_views, wl.N0, g.n_views, 1.0, 0.99, max_epochs))
+        stopped = None
         while k < n_iter:
             e0.record(stream)
-            st = S.step(x, bb)
+            try:
+                st = S.step(x, bb)
+            except fbl.FblError as ex:
+                # e.g. no trial passes (2.3) within the backtrack cap: the solver
+                # keeps x, and this configuration stops here
+                torch.cuda.synchronize(device)
+                stopped = {"iteration": k + 1, "seconds": elapsed, "error": str(ex)}
+                F, _, re = fbl.evaluate(G, x.float() if bf16 else x, b, wl.mu, x_true=xt_d)
+                hist.append((k, elapsed, F, re))
+                break
             e1.record(stream)
             torch.cuda.synchronize(device)
             elapsed += e0.elapsed_time(e1) * 1e-3
@@ -753,9 +763,9 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None, de
                 if target is not None and F <= target:
                     break
         del S, x
-        return hist, trials / max(k, 1)
+        return hist, trials / max(k, 1), stopped
 
-    plain, plain_trials = run(False, False, False, epochs)
+    plain, plain_trials, plain_stop = run(False, False, False, epochs)
     F_star = plain[-1][2]
     target = F_star * (1.0 + 1e-3)
     plain_hit = next(h for h in plain if h[2] <= target)
@@ -765,17 +775,21 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None, de
            "plain_trials_per_iteration": plain_trials,
            "check_every_iterations": check_every, "proposal_margin": 0.25,
            "proposal_traces": meta.get("traces")}
+    if plain_stop:
+        out["plain_stopped"] = plain_stop
     configs = [("fast", True, True, True)]
     if decompose:
         configs += [("learned_only", True, False, False), ("bf16_only", False, True, False),
                     ("graph_only", False, False, True)]
     for name, learned, bf16, graph in configs:
-        h, tr = run(learned, bf16, graph, 2 * epochs, target)
+        h, tr, stop = run(learned, bf16, graph, 2 * epochs, target)
         hit = next((r for r in h if r[2] <= target), None)
         rec = {"learned_proposal": learned, "bf16_storage": bf16, "graph_captured": graph,
                "s": hit[1] if hit else None, "iterations": hit[0] if hit else None,
                "trials_per_iteration": tr, "rel_error_vs_x_true": hit[3] if hit and xt is not None else None,
                "speedup": (plain_hit[1] / hit[1]) if hit else None}
+        if stop:
+            rec["stopped"] = stop
         if name == "fast":
             out["fast"] = "learned proposal + BF16 storage + graph-captured iteration"
             out["fast_s"] = rec["s"]
@@ -783,6 +797,8 @@ def time_to_objective(fbl, G, g, wl, b, device, epochs, check_every, xt=None, de
             out["fast_trials_per_iteration"] = tr
             out["fast_rel_error_vs_x_true"] = rec["rel_error_vs_x_true"]
             out["speedup"] = rec["speedup"]
+            if stop:
+                out["fast_stopped"] = stop
         else:
             out[name] = rec
     del b16
